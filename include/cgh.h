@@ -1,0 +1,213 @@
+/*
+ * cgh.h -- C ABI of the GB300 (sm_103a) hot path of complex-valued 2D Gaussian hologram
+ * optimisation (arXiv 2511.15022).
+ *
+ * The problem (Sec. 3, "Problem Definition"): given pre-activation Gaussian parameters
+ * G_n = {x~_n, s~_n, theta_n, c_n, phi_n, alpha~_n} (Sec. 3.1), wavelengths, pixel pitch,
+ * plane distances d_l and target intensities I^_l in R^{C x H x W}, render the complex
+ * field U(0) = H in C^{C x H x W} (Algorithm 2), propagate it to every plane with the
+ * band-limited angular spectrum method (Algorithm 3 and Sec. 2: zero-pad, FFT, multiply
+ * by H_d, inverse FFT, crop), take the intensity loss L_MSE = 1/L sum_l ||I_l - I^_l||^2
+ * with I_l = |U(d_l)|^2 (Sec. 3.2; mean over C*H*W pixels), and run the backward pass
+ * through both steps (Suppl. gradients, Suppl. BLASM backward with conj(H)).
+ *
+ * Conventions shared by every entry point
+ *   - Every array argument is a DEVICE pointer owned by the caller, except where a
+ *     parameter says "host".  The library never frees caller memory.
+ *   - Device work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = the
+ *     legacy default stream) and is asynchronous; a return of CGH_OK means the work was
+ *     enqueued, not that it finished.  Launch errors are reported as CGH_ERR_CUDA.
+ *   - Floating point is FP32.  Complex arrays are interleaved (re, im) float pairs
+ *     (CUDA float2, 8-byte aligned).  Field layout [C][H][W] row-major; multi-plane
+ *     layout [L][C][H][W].  Gradients w.r.t. a complex array hold (dL/dRe, dL/dIm).
+ *   - Parameters are structure-of-arrays in pre-activation form (Sec. 3.1):
+ *     xy_raw[N][2], s_raw[N][2], theta[N], amp[N][C], phase[N][C], alpha_raw[N].
+ *     Activations (Suppl.): x = (tanh(x~)+1)/2 * (W, H), s = exp(s~) + 0.1,
+ *     alpha = sigmoid(alpha~).  Pixel centres are the integers 0..W-1, 0..H-1.
+ *   - Errors: every function returns a cgh_status; no exception crosses the ABI.
+ *     cgh_last_error_string() gives a human-readable detail for the calling thread.
+ *   - A plan is not thread-safe: one plan is driven from one host thread at a time, and
+ *     calls that share a plan's workspace must be ordered on one stream.
+ */
+#ifndef CGH_H
+#define CGH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CGH_OK = 0,
+  CGH_ERR_ARG = 1,              /* invalid argument (null pointer, bad size, ...) */
+  CGH_ERR_CUDA = 2,             /* a CUDA runtime call or kernel launch failed */
+  CGH_ERR_TIMEOUT = 3,          /* a bounded device-side wait expired */
+  CGH_ERR_NONFINITE = 4,        /* non-finite parameter seen (reported by cgh_plan_status) */
+  CGH_ERR_UNSUPPORTED_SIZE = 5, /* padded FFT length has a prime factor > 5, or C > 4 */
+  CGH_ERR_WORKSPACE = 6,        /* no workspace attached, or it is too small */
+  CGH_ERR_CAPACITY = 7          /* N exceeds the plan's max_gaussians */
+} cgh_status;
+
+typedef struct cgh_plan cgh_plan;
+
+/* Pre-activation Gaussian parameters (device pointers, layouts above). */
+typedef struct {
+  int32_t N;
+  const float* xy_raw;
+  const float* s_raw;
+  const float* theta;
+  const float* amp;
+  const float* phase;
+  const float* alpha_raw;
+} cgh_params;
+
+/* Gradients of the pre-activation parameters (device pointers, same layouts).  Every
+ * array is overwritten (not accumulated). */
+typedef struct {
+  float* xy_raw;
+  float* s_raw;
+  float* theta;
+  float* amp;
+  float* phase;
+  float* alpha_raw;
+} cgh_grads;
+
+/* Create a plan for one hologram geometry.
+ *   H, W           image size in pixels (>= 1)
+ *   C              colour channels, 1..4; lambda_m[C] (host) wavelengths in metres
+ *   L              target planes (>= 1); z_m[L] (host) propagation distances in metres
+ *   pad_factor     zero-pad factor of Alg. 1 "ZeroPad" (the padded grid is
+ *                  pad_factor*H x pad_factor*W with the image centred at
+ *                  ((pad*H-H)/2, (pad*W-W)/2)); both padded sizes must factor into 2,3,5
+ *   pitch_m        pixel pitch in metres
+ *   aperture       optional circular aperture radius in frequency-index units
+ *                  (Algorithm 3; 0 disables it)
+ *   cutoff         effective-opacity skip threshold of Algorithm 2 (1/255 in the paper;
+ *                  0 keeps every pair -- "smooth mode")
+ *   max_gaussians  largest N the plan will be called with (sizes the workspace)
+ * The plan owns only host memory and small device tables (twiddles, transfer-function
+ * constants); bulk scratch is the caller-provided workspace (cgh_plan_set_workspace). */
+cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L, int32_t pad_factor,
+                           const double* lambda_m, double pitch_m, const double* z_m,
+                           double aperture, float cutoff, int32_t max_gaussians,
+                           cgh_plan** out_plan);
+
+cgh_status cgh_plan_destroy(cgh_plan* plan);
+
+/* Bytes of device workspace the plan needs (host output). */
+cgh_status cgh_plan_workspace_bytes(const cgh_plan* plan, size_t* out_bytes);
+
+/* Attach a caller-owned device workspace (256-byte aligned, >= the size above).  It must
+ * stay valid until it is replaced or the plan is destroyed. */
+cgh_status cgh_plan_set_workspace(cgh_plan* plan, void* workspace, size_t bytes);
+
+/* Tuning knobs (host input).  Zero fields keep the current value.
+ *   col_block    columns per CTA in the column FFT passes (1, 2, 4 or 8)
+ *   row_block    rows per CTA in the row FFT passes (1..8)
+ *   fft_threads  threads per CTA of the FFT passes (128..1024)
+ *   pair_capacity_per_gaussian  (Gaussian, tile) list capacity as a multiple of N */
+typedef struct {
+  int32_t col_block;
+  int32_t row_block;
+  int32_t fft_threads;
+  int32_t pair_capacity_per_gaussian;
+} cgh_tuning;
+
+cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* tuning);
+cgh_status cgh_plan_get_tuning(const cgh_plan* plan, cgh_tuning* out);
+
+/* Per-(channel, plane) band-limit bounds of Algorithm 3 (host outputs [C*L] each): the
+ * largest |signed frequency index| that passes |f_x| < f_x^max (resp. y), index c*L + l.
+ * Computed on the host in FP64 exactly as the definition reads. */
+cgh_status cgh_plan_band_limits(const cgh_plan* plan, int32_t* kx_max, int32_t* ky_max);
+
+/* Synchronous status read of the last raster call on this plan (blocks on `stream`):
+ * pairs_needed = (Gaussian, tile) pairs of the last binning, overflow = 1 if that
+ * exceeded the list capacity (tiles past it were rendered by the exhaustive path, still
+ * exact), nonfinite = 1 if a non-finite parameter was seen (those Gaussians were
+ * skipped).  Any output pointer may be NULL. */
+cgh_status cgh_plan_status(cgh_plan* plan, int64_t* pairs_needed, int32_t* overflow,
+                           int32_t* nonfinite, void* stream);
+
+/* Forward rasterisation, Algorithm 2 with the per-pixel sum of Sec. 3.1:
+ *   U_c(p) = sum_n c_{n,c} a_n(p) exp(j phi_{n,c}),  a_n(p) = min(0.99, alpha_n G_n(p)),
+ *   G_n(p) = exp(max(-1/2 (p-x_n)^T Sigma_n^{-1} (p-x_n), -50)), pairs with a < cutoff
+ *   skipped.  U_out: [C][H][W] complex. */
+cgh_status cgh_raster_fwd(cgh_plan* plan, const cgh_params* params, void* U_out,
+                          void* stream);
+
+/* Backward rasterisation (Suppl. "Detailed Gradient Derivation"): given dU = dL/dU
+ * [C][H][W] complex, writes the gradients of all pre-activation parameters.  The
+ * Gaussian values are recomputed; no forward state is needed. */
+cgh_status cgh_raster_bwd(cgh_plan* plan, const cgh_params* params, const void* dU,
+                          const cgh_grads* grads, void* stream);
+
+/* BLASM forward (Algorithm 3 inside Alg. 1 "ZeroPad" + "MultiPlanePropagate"):
+ *   Ud[l][c] = crop(IFFT2(H_{c,l} . FFT2(pad(U0[c])))) / (Ny*Nx normalisation).
+ * U0: [C][H][W] complex;  Ud_out: [L][C][H][W] complex. */
+cgh_status cgh_blasm_fwd(cgh_plan* plan, const void* U0, void* Ud_out, void* stream);
+
+/* BLASM backward (Suppl. BLASM "Backward Pass", conj(H) under the same band limit):
+ *   dU0[c] = sum_l crop(IFFT2(conj(H_{c,l}) . FFT2(pad(dUd[l][c])))).
+ * dUd: [L][C][H][W] complex;  dU0_out: [C][H][W] complex. */
+cgh_status cgh_blasm_bwd(cgh_plan* plan, const void* dUd, void* dU0_out, void* stream);
+
+/* Intensity loss (Sec. 3.2 L_MSE): loss = 1/(L*C*H*W) sum (|Ud|^2 - target)^2 written to
+ * loss_out (device float[1]); dUd_out (may be NULL) receives dL/dUd = 4 (|Ud|^2 - target)
+ * / (L*C*H*W) * Ud.  Ud: [L][C][H][W] complex; target: [L][C][H][W] float. */
+cgh_status cgh_intensity_loss(cgh_plan* plan, const void* Ud, const float* target,
+                              float* loss_out, void* dUd_out, void* stream);
+
+/* Forward only: raster -> BLASM -> loss (loss_out: device float[1]).  Nothing but the
+ * workspace is written. */
+cgh_status cgh_forward_loss(cgh_plan* plan, const cgh_params* params, const float* target,
+                            float* loss_out, void* stream);
+
+/* One fused forward + backward pass of the whole path (Algorithm 1 loop body without
+ * the optimiser): raster -> pad -> FFT -> x H_{c,l} for all planes -> IFFT -> crop ->
+ * |U|^2 -> loss -> dL/dU -> adjoint propagation -> raster backward.  Writes loss_out
+ * (device float[1]) and all gradients. */
+cgh_status cgh_step(cgh_plan* plan, const cgh_params* params, const float* target,
+                    float* loss_out, const cgh_grads* grads, void* stream);
+
+/* One Adam step over up to 8 parameter groups in a single launch (PyTorch semantics, no
+ * weight decay): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr/(1-b1^t) * m / (sqrt(v)/sqrt(1-b2^t) + eps).  step >= 1.  The paper uses
+ * Adan with per-group learning rates (Sec. 4); this is the Adam variant with the same
+ * per-group rates. */
+typedef struct {
+  float* param;
+  const float* grad;
+  float* exp_avg;
+  float* exp_avg_sq;
+  int64_t count;
+  float lr;
+} cgh_adam_group;
+
+cgh_status cgh_adam_step(const cgh_adam_group* groups /* host array */, int32_t num_groups,
+                         int32_t step, float beta1, float beta2, float eps, void* stream);
+
+/* Number of kernels launched by this thread's calls into the library so far (host
+ * counter; used to report launches per step). */
+int64_t cgh_launch_count(void);
+
+/* Per-kernel timing with CUDA events recorded on each kernel's own launch stream.
+ * cgh_profile_enable(1) starts recording (at most 65536 launches per window; later ones
+ * are not timed); cgh_profile_collect() waits for the recorded events, writes per kernel
+ * id the summed milliseconds and launch counts (arrays of cgh_kernel_count() entries,
+ * host outputs) and starts a new window.  cgh_kernel_name(id) names a kernel id.
+ * Profiling records events and must not be enabled during CUDA-graph capture. */
+cgh_status cgh_profile_enable(int32_t enable);
+cgh_status cgh_profile_collect(double* total_ms, int64_t* launches);
+int32_t cgh_kernel_count(void);
+const char* cgh_kernel_name(int32_t id);
+
+const char* cgh_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGH_H */

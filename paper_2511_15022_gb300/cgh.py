@@ -1,0 +1,331 @@
+"""Thin Python binding of libcgh (include/cgh.h): argument marshalling only.
+
+Every array is a CUDA torch tensor whose pointer is handed to the C ABI; all arithmetic
+runs in the library's sm_103a kernels.  There is no CPU fallback: if the library or a GPU
+is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+PARAM_KEYS = ("xy_raw", "s_raw", "theta", "amp", "phase", "alpha_raw")
+
+_lib = None
+
+
+class CGHError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in PARAM_KEYS]
+
+
+class _Grads(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in PARAM_KEYS]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("col_block", ctypes.c_int32), ("row_block", ctypes.c_int32),
+                ("fft_threads", ctypes.c_int32), ("pair_capacity_per_gaussian", ctypes.c_int32)]
+
+
+class _AdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+                ("exp_avg", ctypes.c_void_p), ("exp_avg_sq", ctypes.c_void_p),
+                ("count", ctypes.c_int64), ("lr", ctypes.c_float)]
+
+
+EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
+           "cgh_plan_set_workspace", "cgh_plan_set_tuning", "cgh_plan_get_tuning",
+           "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
+           "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
+           "cgh_step", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
+           "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcgh.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise CGHError(f"libcgh.so not found at {path}; run paper_2511_15022_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, f32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.cgh_plan_create.argtypes = [i32, i32, i32, i32, i32, dp, f64, dp, f64, f32, i32,
+                                    ctypes.POINTER(vp)]
+    lib.cgh_plan_destroy.argtypes = [vp]
+    lib.cgh_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cgh_plan_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.cgh_plan_set_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
+    lib.cgh_plan_get_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
+    lib.cgh_plan_band_limits.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.cgh_plan_status.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32), vp]
+    lib.cgh_raster_fwd.argtypes = [vp, ctypes.POINTER(_Params), vp, vp]
+    lib.cgh_raster_bwd.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Grads), vp]
+    lib.cgh_blasm_fwd.argtypes = [vp, vp, vp, vp]
+    lib.cgh_blasm_bwd.argtypes = [vp, vp, vp, vp]
+    lib.cgh_intensity_loss.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.cgh_forward_loss.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp]
+    lib.cgh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads), vp]
+    lib.cgh_adam_step.argtypes = [ctypes.POINTER(_AdamGroup), i32, i32, f32, f32, f32, vp]
+    lib.cgh_launch_count.restype = i64
+    lib.cgh_last_error_string.restype = ctypes.c_char_p
+    lib.cgh_profile_enable.argtypes = [i32]
+    lib.cgh_profile_collect.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.cgh_kernel_count.restype = i32
+    lib.cgh_kernel_name.argtypes = [i32]
+    lib.cgh_kernel_name.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("cgh_launch_count", "cgh_last_error_string", "cgh_kernel_count",
+                        "cgh_kernel_name"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = _lib.cgh_last_error_string().decode(errors="replace")
+        raise CGHError(f"{what} failed with status {status}: {msg}")
+
+
+def _stream(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _need(t: torch.Tensor, dtype: torch.dtype, shape, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise CGHError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise CGHError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise CGHError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise CGHError(f"{name} must be contiguous")
+
+
+def launch_count() -> int:
+    return int(load().cgh_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Start (or stop) per-kernel CUDA-event timing inside the library."""
+    lib = load()
+    _check(lib.cgh_profile_enable(1 if on else 0), "cgh_profile_enable")
+
+
+def profile_collect() -> Dict[str, dict]:
+    """Per-kernel {ms, launches} since the last collect (waits for the recorded events)."""
+    lib = load()
+    n = int(lib.cgh_kernel_count())
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _check(lib.cgh_profile_collect(ms, cnt), "cgh_profile_collect")
+    return {lib.cgh_kernel_name(i).decode(): {"ms": float(ms[i]), "launches": int(cnt[i])}
+            for i in range(n) if cnt[i] > 0}
+
+
+class Plan:
+    """One hologram geometry: H x W pixels, C wavelengths, L planes (cgh_plan_create)."""
+
+    def __init__(self, H: int, W: int, wavelengths_m: Sequence[float], pitch_m: float,
+                 z_m: Sequence[float], pad: int = 2, aperture: float = 0.0,
+                 cutoff: float = 1.0 / 255.0, max_gaussians: int = 1 << 16,
+                 device: Optional[torch.device] = None, tuning: Optional[dict] = None):
+        lib = load()
+        self.H, self.W = int(H), int(W)
+        self.C, self.L = len(wavelengths_m), len(z_m)
+        self.wavelengths_m = tuple(float(v) for v in wavelengths_m)
+        self.z_m = tuple(float(v) for v in z_m)
+        self.pitch_m, self.pad, self.cutoff = float(pitch_m), int(pad), float(cutoff)
+        self.aperture = float(aperture)
+        self.max_gaussians = int(max_gaussians)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        lam = (ctypes.c_double * self.C)(*self.wavelengths_m)
+        zz = (ctypes.c_double * self.L)(*self.z_m)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.cgh_plan_create(self.H, self.W, self.C, self.L, self.pad, lam,
+                                       self.pitch_m, zz, self.aperture, self.cutoff,
+                                       self.max_gaussians, ctypes.byref(h)), "cgh_plan_create")
+        self._h = h
+        self._ws = None
+        if tuning:
+            self.set_tuning(**tuning)
+        self._attach_workspace()
+
+    def _attach_workspace(self):
+        n = ctypes.c_size_t()
+        _check(_lib.cgh_plan_workspace_bytes(self._h, ctypes.byref(n)), "workspace_bytes")
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.device)
+        _check(_lib.cgh_plan_set_workspace(self._h, ctypes.c_void_p(self._ws.data_ptr()),
+                                           self._ws.numel()), "set_workspace")
+
+    @property
+    def workspace_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(_lib.cgh_plan_workspace_bytes(self._h, ctypes.byref(n)), "workspace_bytes")
+        return int(n.value)
+
+    def set_tuning(self, col_block=0, row_block=0, fft_threads=0, pair_capacity_per_gaussian=0):
+        t = _Tuning(col_block, row_block, fft_threads, pair_capacity_per_gaussian)
+        _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
+        if self._ws is not None:
+            self._attach_workspace()
+
+    def get_tuning(self) -> dict:
+        t = _Tuning()
+        _check(_lib.cgh_plan_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
+        return {k: getattr(t, k) for k, _ in _Tuning._fields_}
+
+    def band_limits(self):
+        kx = (ctypes.c_int32 * (self.C * self.L))()
+        ky = (ctypes.c_int32 * (self.C * self.L))()
+        _check(_lib.cgh_plan_band_limits(self._h, kx, ky), "band_limits")
+        return list(kx), list(ky)
+
+    def status(self, stream=None) -> dict:
+        pairs, ov, nf = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.cgh_plan_status(self._h, ctypes.byref(pairs), ctypes.byref(ov),
+                                    ctypes.byref(nf), ctypes.c_void_p(_stream(stream))), "status")
+        return {"pairs": int(pairs.value), "overflow": bool(ov.value), "nonfinite": bool(nf.value)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.cgh_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- marshalling helpers
+    def _params(self, p: Dict[str, torch.Tensor]) -> _Params:
+        N = int(p["theta"].shape[0])
+        shapes = {"xy_raw": (N, 2), "s_raw": (N, 2), "theta": (N,), "amp": (N, self.C),
+                  "phase": (N, self.C), "alpha_raw": (N,)}
+        for k in PARAM_KEYS:
+            _need(p[k], torch.float32, shapes[k], k)
+        return _Params(N, *[ctypes.c_void_p(p[k].data_ptr()) for k in PARAM_KEYS])
+
+    def empty_grads(self, N: int) -> Dict[str, torch.Tensor]:
+        d = self.device
+        return {"xy_raw": torch.empty(N, 2, device=d), "s_raw": torch.empty(N, 2, device=d),
+                "theta": torch.empty(N, device=d), "amp": torch.empty(N, self.C, device=d),
+                "phase": torch.empty(N, self.C, device=d), "alpha_raw": torch.empty(N, device=d)}
+
+    def _grads(self, g: Dict[str, torch.Tensor], N: int) -> _Grads:
+        shapes = {"xy_raw": (N, 2), "s_raw": (N, 2), "theta": (N,), "amp": (N, self.C),
+                  "phase": (N, self.C), "alpha_raw": (N,)}
+        for k in PARAM_KEYS:
+            _need(g[k], torch.float32, shapes[k], "grad " + k)
+        return _Grads(*[ctypes.c_void_p(g[k].data_ptr()) for k in PARAM_KEYS])
+
+    # -- entry points (same names as the C ABI)
+    def raster_fwd(self, params, out=None, stream=None) -> torch.Tensor:
+        prm = self._params(params)
+        U = out if out is not None else torch.empty(self.C, self.H, self.W, dtype=torch.complex64,
+                                                    device=self.device)
+        _need(U, torch.complex64, (self.C, self.H, self.W), "U_out")
+        _check(_lib.cgh_raster_fwd(self._h, ctypes.byref(prm), ctypes.c_void_p(U.data_ptr()),
+                                   ctypes.c_void_p(_stream(stream))), "cgh_raster_fwd")
+        return U
+
+    def raster_bwd(self, params, dU, grads=None, stream=None) -> Dict[str, torch.Tensor]:
+        prm = self._params(params)
+        _need(dU, torch.complex64, (self.C, self.H, self.W), "dU")
+        g = grads if grads is not None else self.empty_grads(prm.N)
+        gs = self._grads(g, prm.N)
+        _check(_lib.cgh_raster_bwd(self._h, ctypes.byref(prm), ctypes.c_void_p(dU.data_ptr()),
+                                   ctypes.byref(gs), ctypes.c_void_p(_stream(stream))),
+               "cgh_raster_bwd")
+        return g
+
+    def blasm_fwd(self, U0, out=None, stream=None) -> torch.Tensor:
+        _need(U0, torch.complex64, (self.C, self.H, self.W), "U0")
+        Ud = out if out is not None else torch.empty(self.L, self.C, self.H, self.W,
+                                                     dtype=torch.complex64, device=self.device)
+        _need(Ud, torch.complex64, (self.L, self.C, self.H, self.W), "Ud_out")
+        _check(_lib.cgh_blasm_fwd(self._h, ctypes.c_void_p(U0.data_ptr()),
+                                  ctypes.c_void_p(Ud.data_ptr()), ctypes.c_void_p(_stream(stream))),
+               "cgh_blasm_fwd")
+        return Ud
+
+    def blasm_bwd(self, dUd, out=None, stream=None) -> torch.Tensor:
+        _need(dUd, torch.complex64, (self.L, self.C, self.H, self.W), "dUd")
+        dU0 = out if out is not None else torch.empty(self.C, self.H, self.W,
+                                                      dtype=torch.complex64, device=self.device)
+        _need(dU0, torch.complex64, (self.C, self.H, self.W), "dU0_out")
+        _check(_lib.cgh_blasm_bwd(self._h, ctypes.c_void_p(dUd.data_ptr()),
+                                  ctypes.c_void_p(dU0.data_ptr()), ctypes.c_void_p(_stream(stream))),
+               "cgh_blasm_bwd")
+        return dU0
+
+    def intensity_loss(self, Ud, target, want_grad=True, stream=None):
+        _need(Ud, torch.complex64, (self.L, self.C, self.H, self.W), "Ud")
+        _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        dUd = torch.empty_like(Ud) if want_grad else None
+        _check(_lib.cgh_intensity_loss(self._h, ctypes.c_void_p(Ud.data_ptr()),
+                                       ctypes.c_void_p(target.data_ptr()),
+                                       ctypes.c_void_p(loss.data_ptr()),
+                                       ctypes.c_void_p(dUd.data_ptr() if dUd is not None else 0),
+                                       ctypes.c_void_p(_stream(stream))), "cgh_intensity_loss")
+        return loss, dUd
+
+    def forward_loss(self, params, target, loss_out=None, stream=None) -> torch.Tensor:
+        prm = self._params(params)
+        _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
+        loss = loss_out if loss_out is not None else torch.empty(1, dtype=torch.float32,
+                                                                 device=self.device)
+        _check(_lib.cgh_forward_loss(self._h, ctypes.byref(prm), ctypes.c_void_p(target.data_ptr()),
+                                     ctypes.c_void_p(loss.data_ptr()),
+                                     ctypes.c_void_p(_stream(stream))), "cgh_forward_loss")
+        return loss
+
+    def step(self, params, target, grads=None, loss_out=None, stream=None):
+        """Fused forward + backward (cgh_step).  Returns (loss[1], grads)."""
+        prm = self._params(params)
+        _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
+        g = grads if grads is not None else self.empty_grads(prm.N)
+        gs = self._grads(g, prm.N)
+        loss = loss_out if loss_out is not None else torch.empty(1, dtype=torch.float32,
+                                                                 device=self.device)
+        _check(_lib.cgh_step(self._h, ctypes.byref(prm), ctypes.c_void_p(target.data_ptr()),
+                             ctypes.c_void_p(loss.data_ptr()), ctypes.byref(gs),
+                             ctypes.c_void_p(_stream(stream))), "cgh_step")
+        return loss, g
+
+
+def adam_step(groups, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Fused Adam over up to 8 groups: each group is (param, grad, exp_avg, exp_avg_sq, lr)."""
+    lib = load()
+    arr = (_AdamGroup * len(groups))()
+    for i, (p, g, m, v, lr) in enumerate(groups):
+        for t, name in ((p, "param"), (g, "grad"), (m, "exp_avg"), (v, "exp_avg_sq")):
+            _need(t, torch.float32, tuple(p.shape), name)
+        arr[i] = _AdamGroup(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(),
+                            float(lr))
+    _check(lib.cgh_adam_step(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
+                             ctypes.c_void_p(_stream(stream))), "cgh_adam_step")

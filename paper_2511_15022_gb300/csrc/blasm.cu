@@ -1,0 +1,431 @@
+// blasm.cu -- band-limited angular spectrum propagation as fused row/column FFT passes.
+//
+// The 2D transform of the zero-padded Ny x Nx grid (Ny = pad*H, Nx = pad*W) is split into
+// row and column passes that never materialise the padded grid:
+//   rows_pad_fwd    pad each image row into the Nx-long row (zeros outside the centred
+//                   window) and FFT it; only the H rows that hold data are transformed.
+//                   Output: the "half grid" H x Nx.
+//   cols_fwd_planes per column block: pad the column to Ny, FFT, keep the spectrum in
+//                   shared memory and for every plane l multiply by H_{c,l} (Algorithm 3:
+//                   band limit, k_z, exp(j k_z d), optional aperture) / (Ny Nx), inverse
+//                   FFT and keep the H cropped rows.  Output: L half grids.
+//   rows_loss       per plane and row: inverse row FFT, crop, I = |U|^2, loss partials
+//                   (I - I^)^2, seed dL/dU = 4 (I - I^) U / (L C H W), re-pad and forward
+//                   row FFT -- written back in place.
+//   cols_bwd_planes per column block: for every plane FFT the column, multiply by
+//                   conj(H_{c,l}) / (Ny Nx) and accumulate, inverse FFT once, crop.
+//   rows_inv_crop   inverse row FFT and crop back to H x W.
+// Half grids are stored column-blocked: element (row r, column k) of a half grid lives at
+// ((k / CB) * H + r) * CB + k % CB, so a column pass reads one contiguous slab and a row
+// pass of RB rows reads/writes runs of RB * CB complex values.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cgh_internal.h"
+#include "fft.cuh"
+
+namespace cgh {
+
+__device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+
+// H_{c,l}(s_x, s_y) * scale, Algorithm 3.  Phase k_z d / 2 pi is evaluated as
+// frac(d / lambda) - (d/lambda) q / (1 + sqrt(1 - q)) with q = lambda^2 (f_x^2 + f_y^2)
+// (the same value as (d / lambda) sqrt(1 - q); the large integer number of turns is removed
+// on the host in FP64).  Evanescent bins inside the band get k_z = 0 (H = 1).
+__device__ __forceinline__ float2 transfer(const BlasmDev& bl, int cl, int sx, int sy,
+                                           float scale) {
+  const TFConst& t = bl.tf[cl];
+  if (abs(sx) > t.kx_max || abs(sy) > t.ky_max) return make_float2(0.f, 0.f);
+  if (bl.aperture2 > 0.f) {
+    const float ax = (float)sx + 0.5f, ay = (float)sy + 0.5f;
+    if (ax * ax + ay * ay >= bl.aperture2) return make_float2(0.f, 0.f);
+  }
+  const float fx2 = (float)(sx * sx), fy2 = (float)(sy * sy);
+  const float q = fmaf(t.qx, fx2, t.qy * fy2);
+  float turns = 0.f;
+  if (q < 1.f) {
+    const float den = 1.f + sqrtf(1.f - q);
+    const float num = fmaf(t.ax, fx2, t.ay * fy2);
+    turns = t.turns0 - num / den;
+    turns -= rintf(turns);
+  }
+  float s, c;
+  sincospif(2.f * turns, &s, &c);
+  return make_float2(c * scale, s * scale);
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(512, 1) k_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
+                                                       const FFTDesc fx, int RB, int CB, int bs,
+                                                       const float2* __restrict__ in,
+                                                       float2* __restrict__ half) {
+  extern __shared__ float2 sm[];
+  const int batch = blockIdx.y;
+  const int y0 = blockIdx.x * RB;
+  const int rows = min(RB, bl.H - y0);
+  const int Nx = bl.Nx, W = bl.W, H = bl.H;
+  const float2* src = in + (size_t)batch * H * W;
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int b = idx / Nx, k = idx - b * Nx;
+    const int x = k - bl.ox;
+    float2 v = make_float2(0.f, 0.f);
+    if (x >= 0 && x < W) v = src[(size_t)(y0 + b) * W + x];
+    sm[b * bs + sidx(k)] = v;
+  }
+  __syncthreads();
+  block_fft<false, MAXB>(sm, bs, rows, fx);
+  float2* dst = half + (size_t)batch * H * Nx;
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int kk = idx % CB, rest = idx / CB;
+    const int b = rest % rows, kb = rest / rows;
+    dst[((size_t)kb * H + y0 + b) * CB + kk] = sm[b * bs + sidx(kb * CB + kk)];
+  }
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(512, 1) k_cols_fwd_planes(const __grid_constant__ BlasmDev bl,
+                                                          const FFTDesc fy, int CB, int bs,
+                                                          const float2* __restrict__ Y,
+                                                          float2* __restrict__ V) {
+  extern __shared__ float2 sm[];
+  float2* S = sm;
+  float2* Wk = sm + CB * bs;
+  const int c = blockIdx.y, kb = blockIdx.x;
+  const int H = bl.H, Ny = bl.Ny, Nx = bl.Nx, C = bl.C, oy = bl.oy;
+  const float2* src = Y + (size_t)c * H * Nx + (size_t)kb * H * CB;
+  for (int idx = threadIdx.x; idx < CB * Ny; idx += blockDim.x) {
+    const int b = idx % CB, i = idx / CB;
+    const int y = i - oy;
+    S[b * bs + sidx(i)] = (y >= 0 && y < H) ? src[(size_t)y * CB + b] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  block_fft<false, MAXB>(S, bs, CB, fy);
+  for (int l = 0; l < bl.L; ++l) {
+    const int cl = c * bl.L + l;
+    for (int idx = threadIdx.x; idx < CB * Ny; idx += blockDim.x) {
+      const int b = idx / Ny, i = idx - b * Ny;
+      const int sx = signed_index(kb * CB + b, Nx), sy = signed_index(i, Ny);
+      const int a = b * bs + sidx(i);
+      Wk[a] = cmul(S[a], transfer(bl, cl, sx, sy, bl.inv_ntot));
+    }
+    __syncthreads();
+    block_fft<true, MAXB>(Wk, bs, CB, fy);
+    float2* dst = V + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB;
+    for (int idx = threadIdx.x; idx < CB * H; idx += blockDim.x) {
+      const int b = idx % CB, y = idx / CB;
+      dst[(size_t)y * CB + b] = Wk[b * bs + sidx(oy + y)];
+    }
+    __syncthreads();
+  }
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(512, 1) k_rows_inv_crop(const __grid_constant__ BlasmDev bl,
+                                                        const FFTDesc fx, int RB, int CB, int bs,
+                                                        const float2* __restrict__ half,
+                                                        float2* __restrict__ out) {
+  extern __shared__ float2 sm[];
+  const int batch = blockIdx.y;
+  const int y0 = blockIdx.x * RB;
+  const int rows = min(RB, bl.H - y0);
+  const int Nx = bl.Nx, W = bl.W, H = bl.H;
+  const float2* src = half + (size_t)batch * H * Nx;
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int kk = idx % CB, rest = idx / CB;
+    const int b = rest % rows, kb = rest / rows;
+    sm[b * bs + sidx(kb * CB + kk)] = src[((size_t)kb * H + y0 + b) * CB + kk];
+  }
+  __syncthreads();
+  block_fft<true, MAXB>(sm, bs, rows, fx);
+  float2* dst = out + (size_t)batch * H * W;
+  for (int idx = threadIdx.x; idx < rows * W; idx += blockDim.x) {
+    const int b = idx / W, x = idx - b * W;
+    dst[(size_t)(y0 + b) * W + x] = sm[b * bs + sidx(bl.ox + x)];
+  }
+}
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(512, 1) k_rows_loss(const __grid_constant__ BlasmDev bl,
+                                                    const FFTDesc fx, int RB, int CB, int bs,
+                                                    float2* __restrict__ V,
+                                                    const float* __restrict__ target,
+                                                    float* __restrict__ partials, int want_grad) {
+  extern __shared__ float2 sm[];
+  __shared__ float red[32];
+  const int batch = blockIdx.y;  // l * C + c
+  const int y0 = blockIdx.x * RB;
+  const int rows = min(RB, bl.H - y0);
+  const int Nx = bl.Nx, W = bl.W, H = bl.H;
+  float2* half = V + (size_t)batch * H * Nx;
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int kk = idx % CB, rest = idx / CB;
+    const int b = rest % rows, kb = rest / rows;
+    sm[b * bs + sidx(kb * CB + kk)] = half[((size_t)kb * H + y0 + b) * CB + kk];
+  }
+  __syncthreads();
+  block_fft<true, MAXB>(sm, bs, rows, fx);
+  const float gscale = 4.0f / ((float)bl.L * (float)bl.C * (float)H * (float)W);
+  const float* tg = target + (size_t)batch * H * W;
+  float acc = 0.f;
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int b = idx / Nx, k = idx - b * Nx;
+    const int x = k - bl.ox;
+    const int a = b * bs + sidx(k);
+    float2 g = make_float2(0.f, 0.f);
+    if (x >= 0 && x < W) {
+      const float2 u = sm[a];
+      const float I = fmaf(u.x, u.x, u.y * u.y);
+      const float d = I - tg[(size_t)(y0 + b) * W + x];
+      acc = fmaf(d, d, acc);
+      g = cscale(u, gscale * d);
+    }
+    sm[a] = g;
+  }
+  const float tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  if (!want_grad) return;
+  __syncthreads();
+  block_fft<false, MAXB>(sm, bs, rows, fx);
+  for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
+    const int kk = idx % CB, rest = idx / CB;
+    const int b = rest % rows, kb = rest / rows;
+    half[((size_t)kb * H + y0 + b) * CB + kk] = sm[b * bs + sidx(kb * CB + kk)];
+  }
+}
+
+template <int MAXB>
+__global__ void __launch_bounds__(512, 1) k_cols_bwd_planes(const __grid_constant__ BlasmDev bl,
+                                                          const FFTDesc fy, int CB, int bs,
+                                                          const float2* __restrict__ G,
+                                                          float2* __restrict__ D) {
+  extern __shared__ float2 sm[];
+  float2* S = sm;
+  float2* Wk = sm + CB * bs;
+  const int c = blockIdx.y, kb = blockIdx.x;
+  const int H = bl.H, Ny = bl.Ny, Nx = bl.Nx, C = bl.C, oy = bl.oy;
+  for (int l = 0; l < bl.L; ++l) {
+    const float2* src = G + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB;
+    for (int idx = threadIdx.x; idx < CB * Ny; idx += blockDim.x) {
+      const int b = idx % CB, i = idx / CB;
+      const int y = i - oy;
+      Wk[b * bs + sidx(i)] = (y >= 0 && y < H) ? src[(size_t)y * CB + b] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    block_fft<false, MAXB>(Wk, bs, CB, fy);
+    const int cl = c * bl.L + l;
+    for (int idx = threadIdx.x; idx < CB * Ny; idx += blockDim.x) {
+      const int b = idx / Ny, i = idx - b * Ny;
+      const int sx = signed_index(kb * CB + b, Nx), sy = signed_index(i, Ny);
+      const int a = b * bs + sidx(i);
+      const float2 t = cmulc(Wk[a], transfer(bl, cl, sx, sy, bl.inv_ntot));
+      S[a] = (l == 0) ? t : cadd(S[a], t);
+    }
+    __syncthreads();
+  }
+  block_fft<true, MAXB>(S, bs, CB, fy);
+  float2* dst = D + (size_t)c * H * Nx + (size_t)kb * H * CB;
+  for (int idx = threadIdx.x; idx < CB * H; idx += blockDim.x) {
+    const int b = idx % CB, y = idx / CB;
+    dst[(size_t)y * CB + b] = S[b * bs + sidx(oy + y)];
+  }
+}
+
+// Unfused intensity loss for the standalone API: partials per block, optional gradient.
+__global__ void k_loss_pointwise(long long total, float gscale, const float2* __restrict__ Ud,
+                                 const float* __restrict__ target, float* __restrict__ partials,
+                                 float2* __restrict__ dUd) {
+  __shared__ float red[32];
+  float acc = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 u = Ud[i];
+    const float d = fmaf(u.x, u.x, u.y * u.y) - target[i];
+    acc = fmaf(d, d, acc);
+    if (dUd) dUd[i] = cscale(u, gscale * d);
+  }
+  const float tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// loss = sum(partials) / (L C H W), summed in FP64 in a fixed order.
+__global__ void k_loss_finalize(const float* __restrict__ partials, int count, double inv_norm,
+                                float* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += (double)partials[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[0] = (float)(t * inv_norm);
+  }
+}
+
+}  // namespace cgh
+
+using namespace cgh;
+
+namespace {
+
+// shared-memory stride of one transform of length n: n + n/16 swizzle slots, rounded so
+// that consecutive batch slots start 1 (mod 16) complex values apart.
+int smem_stride(int n) {
+  int s = n + n / 16 + 1;
+  while (s % 16 != 1) ++s;
+  return s;
+}
+
+int max_butterflies(const FFTDesc& d, int nb) {
+  int mb = 0;
+  for (int p = 0; p < d.npass; ++p) mb = mb > (d.n / d.radix[p]) * nb ? mb : (d.n / d.radix[p]) * nb;
+  return mb;
+}
+
+
+}  // namespace
+
+// Threads per CTA and butterflies per thread (MAXB) for nb transforms of d: the smallest
+// thread count >= the tuned one that needs at most 2 butterflies per thread per pass.
+LaunchShape fft_shape(const cgh_plan* p, const FFTDesc& d, int nb, int buffers) {
+  const size_t smem = sizeof(float2) * (size_t)smem_stride(d.n) * nb * buffers + 256;
+  if (smem > kMaxSmemBytes) return {0, 0, false};
+  const int mb = max_butterflies(d, nb);
+  for (int t = p->fft_threads; t <= kMaxFFTThreads; t += 32) {
+    const int need = (mb + t - 1) / t;
+    if (need <= 1) return {t, 1, true};
+    if (need <= 2 && t * 2 >= mb) {
+      // prefer one butterfly per thread when a legal thread count allows it
+      if (mb <= kMaxFFTThreads) return {((mb + 31) / 32) * 32, 1, true};
+      return {t, 2, true};
+    }
+  }
+  return {kMaxFFTThreads, 0, false};
+}
+
+namespace {
+
+template <class K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define CGH_DISPATCH_MAXB(kid, maxb, KERNEL, grid, block, smem, stream, ...)                     \
+  do {                                                                                      \
+    cudaError_t _e = cudaSuccess;                                                           \
+    prof_begin(kid, stream);                                                                \
+    switch (maxb) {                                                                         \
+      case 1: _e = set_smem(KERNEL<1>, smem);                                               \
+        if (_e == cudaSuccess) KERNEL<1><<<grid, block, smem, stream>>>(__VA_ARGS__); break; \
+      case 2: _e = set_smem(KERNEL<2>, smem);                                               \
+        if (_e == cudaSuccess) KERNEL<2><<<grid, block, smem, stream>>>(__VA_ARGS__); break; \
+      default: _e = cudaErrorInvalidConfiguration; break;                                   \
+    }                                                                                       \
+    prof_end(kid, stream);                                                                  \
+    if (_e != cudaSuccess) return _e;                                                       \
+  } while (0)
+
+}  // namespace
+
+int rows_loss_blocks(const cgh_plan* p) {
+  return ((p->H + p->row_block - 1) / p->row_block) * p->L * p->C;
+}
+
+int pointwise_loss_blocks(const cgh_plan* p) {
+  (void)p;
+  return 592;  // 4 blocks of 256 threads per SM on a 148-152 SM part
+}
+
+cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,
+                                cudaStream_t s) {
+  const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
+  LaunchShape sh = fft_shape(p, p->fx, RB, 1);
+  if (!sh.ok) return cudaErrorInvalidConfiguration;
+  dim3 grid((p->H + RB - 1) / RB, batches);
+  const size_t smem = sizeof(float2) * (size_t)bs * RB;
+  CGH_DISPATCH_MAXB(KID_ROWS_PAD_FWD, sh.maxb, k_rows_pad_fwd, grid, sh.threads, smem, s, p->bl, p->fx, RB, CB,
+                    bs, in, half);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s) {
+  const int CB = p->col_block, bs = smem_stride(p->fy.n);
+  LaunchShape sh = fft_shape(p, p->fy, CB, 2);
+  if (!sh.ok) return cudaErrorInvalidConfiguration;
+  dim3 grid(p->bl.Nx / CB, p->C);
+  const size_t smem = sizeof(float2) * (size_t)bs * CB * 2;
+  CGH_DISPATCH_MAXB(KID_COLS_FWD_PLANES, sh.maxb, k_cols_fwd_planes, grid, sh.threads, smem, s, p->bl, p->fy, CB, bs,
+                    Y, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, int batches,
+                                 cudaStream_t s) {
+  const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
+  LaunchShape sh = fft_shape(p, p->fx, RB, 1);
+  if (!sh.ok) return cudaErrorInvalidConfiguration;
+  dim3 grid((p->H + RB - 1) / RB, batches);
+  const size_t smem = sizeof(float2) * (size_t)bs * RB;
+  CGH_DISPATCH_MAXB(KID_ROWS_INV_CROP, sh.maxb, k_rows_inv_crop, grid, sh.threads, smem, s, p->bl, p->fx, RB, CB,
+                    bs, half, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
+                             cudaStream_t s, bool want_grad) {
+  const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
+  LaunchShape sh = fft_shape(p, p->fx, RB, 1);
+  if (!sh.ok) return cudaErrorInvalidConfiguration;
+  dim3 grid((p->H + RB - 1) / RB, p->L * p->C);
+  const size_t smem = sizeof(float2) * (size_t)bs * RB;
+  CGH_DISPATCH_MAXB(KID_ROWS_LOSS, sh.maxb, k_rows_loss, grid, sh.threads, smem, s, p->bl, p->fx, RB, CB, bs,
+                    V, target, partials, want_grad ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s) {
+  const int CB = p->col_block, bs = smem_stride(p->fy.n);
+  LaunchShape sh = fft_shape(p, p->fy, CB, 2);
+  if (!sh.ok) return cudaErrorInvalidConfiguration;
+  dim3 grid(p->bl.Nx / CB, p->C);
+  const size_t smem = sizeof(float2) * (size_t)bs * CB * 2;
+  CGH_DISPATCH_MAXB(KID_COLS_BWD_PLANES, sh.maxb, k_cols_bwd_planes, grid, sh.threads, smem, s, p->bl, p->fy, CB, bs,
+                    G, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* target,
+                                  float* partials, float2* dUd, cudaStream_t s) {
+  const long long total = (long long)p->L * p->C * p->H * p->W;
+  const float gscale = 4.0f / (float)total;
+  prof_begin(KID_LOSS_POINTWISE, s);
+  k_loss_pointwise<<<pointwise_loss_blocks(p), 256, 0, s>>>(total, gscale, Ud, target, partials,
+                                                           dUd);
+  prof_end(KID_LOSS_POINTWISE, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_finalize(cgh_plan* p, const float* partials, int count, float* out,
+                                 cudaStream_t s) {
+  const double inv = 1.0 / ((double)p->L * p->C * p->H * p->W);
+  prof_begin(KID_LOSS_FINALIZE, s);
+  k_loss_finalize<<<1, 1024, 0, s>>>(partials, count, inv, out);
+  prof_end(KID_LOSS_FINALIZE, s);
+  return cudaGetLastError();
+}

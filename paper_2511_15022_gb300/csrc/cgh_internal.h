@@ -1,0 +1,132 @@
+// cgh_internal.h -- plan structure and kernel launch interfaces shared by the
+// translation units of libcgh.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cgh.h"
+
+#define CGH_MAX_C 4
+#define CGH_MAX_L 16
+#define CGH_MAX_PASSES 6
+#define CGH_TILE 16
+// per-Gaussian raw-gradient slots: 2C (P_c, Q_c) + 6 (SG, Sx, Sy, Sxx, Sxy, Syy)
+#define CGH_RAW_STRIDE 16
+// per-Gaussian render record: 5 float4 (see raster.cu)
+#define CGH_REC_F4 5
+// largest CTA of the FFT passes (their __launch_bounds__)
+constexpr int kMaxFFTThreads = 512;
+// opt-in dynamic shared memory per CTA on sm_103a (227 KB)
+constexpr size_t kMaxSmemBytes = 227 * 1024;
+
+// One 1D transform length: mixed-radix Stockham passes and its twiddle table
+// tw[m] = exp(-2 pi i m / n), m in [0, n), computed on the host in FP64.
+struct FFTDesc {
+  int n;
+  int npass;
+  int radix[CGH_MAX_PASSES];
+  const float2* tw;
+};
+
+// Transfer-function constants of one (channel, plane) pair (Algorithm 3), computed on the
+// host in FP64 and rounded once to FP32:
+//   phase in turns = frac(d/lambda) - (ax*sx^2 + ay*sy^2) / (1 + sqrt(1 - q)),
+//   q = qx*sx^2 + qy*sy^2 (= lambda^2 (f_x^2 + f_y^2)), ax = (d/lambda) qx, ay = (d/lambda) qy,
+// which equals k_z d / 2pi = (d/lambda) sqrt(1 - q) with the large integer part removed
+// exactly on the host.  Bins with |s_x| > kx_max or |s_y| > ky_max are outside the band.
+struct TFConst {
+  float turns0;
+  float qx, qy;
+  float ax, ay;
+  int kx_max, ky_max;
+  int _pad;
+};
+
+struct BlasmDev {
+  int H, W, C, L;
+  int Ny, Nx;      // padded sizes
+  int oy, ox;      // offset of the image window inside the padded grid
+  float inv_ntot;  // 1 / (Ny * Nx)
+  float aperture2; // aperture radius^2 in index units (0 = off)
+  TFConst tf[CGH_MAX_C * CGH_MAX_L];  // index c * L + l
+};
+
+struct cgh_plan {
+  // geometry and optics
+  int H, W, C, L, pad;
+  double lambda[CGH_MAX_C];
+  double z[CGH_MAX_L];
+  double pitch, aperture;
+  float cutoff;
+  int max_gaussians;
+  int tiles_x, tiles_y;
+  // tuning
+  int col_block, row_block, fft_threads, pair_cap_mult;
+  // FFT descriptors (host copies; tw points into tables_dev)
+  FFTDesc fx, fy;
+  BlasmDev bl;
+  // device tables owned by the plan (twiddles)
+  void* tables_dev;
+  size_t tables_bytes;
+  // caller workspace
+  char* ws;
+  size_t ws_bytes;
+  // workspace carve-up (byte offsets)
+  size_t off_rec, off_rect, off_raw, off_tile_count, off_tile_start, off_tile_cursor,
+      off_pairs, off_status, off_loss, off_U0, off_Y, off_V, ws_needed;
+  int64_t pair_capacity;
+  int loss_slots;
+};
+
+// status words in the workspace (int32 each)
+enum { ST_PAIRS_LO = 0, ST_PAIRS_HI = 1, ST_OVERFLOW = 2, ST_NONFINITE = 3, ST_COUNT = 8 };
+
+struct LaunchShape {
+  int threads, maxb;
+  bool ok;
+};
+// blasm.cu: CTA shape for nb transforms of d held in `buffers` shared-memory buffers
+// (ok = false if no shape fits the thread or shared-memory limits)
+LaunchShape fft_shape(const cgh_plan* p, const FFTDesc& d, int nb, int buffers);
+
+// ---- launch interfaces (return cudaError_t of the launch) ----
+// raster.cu
+cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s);
+// rebin = false reuses the binning left in the workspace by the preceding raster_fwd with
+// the same parameters.
+cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* dU,
+                              const cgh_grads* g, cudaStream_t s, bool rebin);
+// blasm.cu
+cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,
+                                cudaStream_t s);
+cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s);
+cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, int batches,
+                                 cudaStream_t s);
+cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
+                             cudaStream_t s, bool want_grad);
+cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s);
+cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* target,
+                                  float* partials, float2* dUd, cudaStream_t s);
+cudaError_t launch_loss_finalize(cgh_plan* p, const float* partials, int count, float* out,
+                                 cudaStream_t s);
+int rows_loss_blocks(const cgh_plan* p);
+int pointwise_loss_blocks(const cgh_plan* p);
+// api.cu
+cudaError_t launch_adam(const cgh_adam_group* groups, int n, int step, float b1, float b2,
+                        float eps, cudaStream_t s);
+
+// host-side launch counter (api.cu)
+void cgh_count_launch(int n);
+
+// kernel ids for the event profiler (profile.cu)
+enum KernelId {
+  KID_PREPROCESS = 0, KID_SCAN_TILES, KID_EMIT, KID_RASTER_FWD, KID_RASTER_BWD,
+  KID_GRAD_FINALIZE, KID_ROWS_PAD_FWD, KID_COLS_FWD_PLANES, KID_ROWS_LOSS,
+  KID_COLS_BWD_PLANES, KID_ROWS_INV_CROP, KID_LOSS_POINTWISE, KID_LOSS_FINALIZE, KID_ADAM,
+  KID_COUNT
+};
+// Bracket one kernel launch: records a CUDA event before and after it on its stream when
+// profiling is enabled; otherwise only the launch counter moves.
+void prof_begin(int kid, cudaStream_t s);
+void prof_end(int kid, cudaStream_t s);

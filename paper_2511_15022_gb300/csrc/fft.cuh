@@ -1,0 +1,293 @@
+// fft.cuh -- shared-memory mixed-radix FFT for one CTA (sm_103a).
+//
+// A CTA holds `nb` independent transforms of length n in shared memory, one per batch
+// slot b, at swizzled addresses sidx(b, i) = b * bs + i + (i >> 4) (the extra slot every
+// 16 complex values breaks the power-of-two strides of the first Stockham pass across
+// the 32 banks).  Each pass of radix R runs the Stockham autosort step (Govindaraju et
+// al., "High performance discrete Fourier transforms on graphics processors", SC'08):
+// butterfly j reads elements j + r n/R, multiplies by exp(-+2 pi i r (j mod Ns) / (Ns R)),
+// runs an R-point DFT in registers and writes (j - j mod Ns) R + (j mod Ns) + r Ns.
+// Passes run in place: every thread first reads and transforms its butterflies (at most
+// MAXB of them), the CTA synchronises, then everybody writes.
+//
+// The R-point DFTs are unrolled at compile time: radices 2, 3, 4, 5 are written out;
+// larger radices are Cooley-Tukey compositions R = A * B whose inner twiddles are
+// compile-time constants (evaluated below from the Taylor series of sin and cos on
+// [0, pi/4], with exact values at multiples of pi/4 so trivial twiddles cost nothing).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+namespace cgh {
+
+// ---------------------------------------------------------------- compile-time trig
+namespace ct {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double sin_series(double x) {
+  double x2 = x * x, term = x, sum = x;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x2 / ((2.0 * k) * (2.0 * k + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double cos_series(double x) {
+  double x2 = x * x, term = 1.0, sum = 1.0;
+  for (int k = 1; k < 14; ++k) {
+    term *= -x2 / ((2.0 * k - 1.0) * (2.0 * k));
+    sum += term;
+  }
+  return sum;
+}
+// cos and sin of 2 pi k / n: quadrant from integers, remainder angle in [0, pi/2)
+// folded to [0, pi/4].
+constexpr void cs2pi(long k, long n, double& c, double& s) {
+  long m = ((k % n) + n) % n;
+  long quad = (4 * m) / n;
+  long rem = 4 * m - quad * n;  // angle = (quad + rem/n) * pi/2
+  double cr = 1.0, sr = 0.0;
+  if (rem != 0) {
+    if (2 * rem <= n) {
+      double x = (kPi / 2.0) * (double)rem / (double)n;
+      cr = cos_series(x);
+      sr = sin_series(x);
+    } else {
+      double x = (kPi / 2.0) * (double)(n - rem) / (double)n;
+      cr = sin_series(x);
+      sr = cos_series(x);
+    }
+  }
+  switch (quad) {
+    case 0: c = cr; s = sr; break;
+    case 1: c = -sr; s = cr; break;
+    case 2: c = -cr; s = -sr; break;
+    default: c = sr; s = -cr; break;
+  }
+}
+constexpr double cos2pi(long k, long n) { double c = 0, s = 0; cs2pi(k, n, c, s); return c; }
+constexpr double sin2pi(long k, long n) { double c = 0, s = 0; cs2pi(k, n, c, s); return s; }
+}  // namespace ct
+
+template <int I, int N, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>());
+    sfor<I + 1, N>(f);
+  }
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 z) {
+  return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+}
+
+// multiply by exp(-+2 pi i K / N) with compile-time K, N (sign: - forward, + inverse)
+template <int K, int N, bool INV>
+__device__ __forceinline__ float2 twmul(float2 x) {
+  constexpr long km = ((long)K % N + N) % N;
+  if constexpr ((8 * km) % N == 0) {
+    constexpr int o8 = (int)((8 * km) / N);
+    constexpr int o = INV ? (8 - o8) % 8 : o8;  // forward angle -2 pi o / 8
+    constexpr float r = 0.70710678118654752440f;
+    if constexpr (o == 0) return x;
+    else if constexpr (o == 1) return make_float2((x.x + x.y) * r, (x.y - x.x) * r);
+    else if constexpr (o == 2) return make_float2(x.y, -x.x);
+    else if constexpr (o == 3) return make_float2((x.y - x.x) * r, -(x.x + x.y) * r);
+    else if constexpr (o == 4) return make_float2(-x.x, -x.y);
+    else if constexpr (o == 5) return make_float2(-(x.x + x.y) * r, (x.x - x.y) * r);
+    else if constexpr (o == 6) return make_float2(-x.y, x.x);
+    else return make_float2((x.x - x.y) * r, (x.x + x.y) * r);
+  } else {
+    constexpr float c = (float)ct::cos2pi(K, N);
+    constexpr float s = INV ? (float)ct::sin2pi(K, N) : -(float)ct::sin2pi(K, N);
+    return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+  }
+}
+
+// ---------------------------------------------------------------- R-point DFT codelets
+template <int R, bool INV>
+struct DFT;
+
+template <bool INV>
+struct DFT<1, INV> {
+  __device__ __forceinline__ static void run(float2 (&)[1]) {}
+};
+
+template <bool INV>
+struct DFT<2, INV> {
+  __device__ __forceinline__ static void run(float2 (&v)[2]) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+
+template <bool INV>
+struct DFT<3, INV> {
+  __device__ __forceinline__ static void run(float2 (&v)[3]) {
+    constexpr float h = 0.86602540378443864676f;  // sin(2 pi / 3)
+    float2 t1 = cadd(v[1], v[2]);
+    float2 t2 = mul_mi<INV>(cscale(csub(v[1], v[2]), h));
+    float2 m = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+    v[0] = cadd(v[0], t1);
+    v[1] = cadd(m, t2);
+    v[2] = csub(m, t2);
+  }
+};
+
+template <bool INV>
+struct DFT<4, INV> {
+  __device__ __forceinline__ static void run(float2 (&v)[4]) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  }
+};
+
+template <bool INV>
+struct DFT<5, INV> {
+  __device__ __forceinline__ static void run(float2 (&v)[5]) {
+    constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+    constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+    constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+    constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+    float2 a = cadd(v[1], v[4]), b = csub(v[1], v[4]);
+    float2 c = cadd(v[2], v[3]), d = csub(v[2], v[3]);
+    float2 x0 = v[0];
+    float2 r1 = make_float2(x0.x + c1 * a.x + c2 * c.x, x0.y + c1 * a.y + c2 * c.y);
+    float2 r2 = make_float2(x0.x + c2 * a.x + c1 * c.x, x0.y + c2 * a.y + c1 * c.y);
+    float2 i1 = mul_mi<INV>(make_float2(s1 * b.x + s2 * d.x, s1 * b.y + s2 * d.y));
+    float2 i2 = mul_mi<INV>(make_float2(s2 * b.x - s1 * d.x, s2 * b.y - s1 * d.y));
+    v[0] = make_float2(x0.x + a.x + c.x, x0.y + a.y + c.y);
+    v[1] = cadd(r1, i1);
+    v[4] = csub(r1, i1);
+    v[2] = cadd(r2, i2);
+    v[3] = csub(r2, i2);
+  }
+};
+
+template <int R>
+struct SplitOf {
+  static constexpr int A = (R % 4 == 0 && R > 4) ? 4 : (R % 2 == 0) ? 2 : (R % 3 == 0) ? 3 : 5;
+  static constexpr int B = R / A;
+};
+
+// Composite R = A * B: input n = B n1 + n2, output k = k1 + A k2.
+template <int R, bool INV>
+struct DFT {
+  static_assert(R % SplitOf<R>::A == 0, "unsupported radix");
+  __device__ __forceinline__ static void run(float2 (&v)[R]) {
+    constexpr int A = SplitOf<R>::A, B = SplitOf<R>::B;
+    float2 u[B][A];
+    sfor<0, B>([&](auto N2) {
+      constexpr int n2 = decltype(N2)::value;
+      float2 t[A];
+      sfor<0, A>([&](auto N1) { t[decltype(N1)::value] = v[B * decltype(N1)::value + n2]; });
+      DFT<A, INV>::run(t);
+      sfor<0, A>([&](auto K1) {
+        constexpr int k1 = decltype(K1)::value;
+        u[n2][k1] = twmul<n2 * k1, R, INV>(t[k1]);
+      });
+    });
+    sfor<0, A>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      float2 t[B];
+      sfor<0, B>([&](auto N2) { t[decltype(N2)::value] = u[decltype(N2)::value][k1]; });
+      DFT<B, INV>::run(t);
+      sfor<0, B>([&](auto K2) { v[k1 + A * decltype(K2)::value] = t[decltype(K2)::value]; });
+    });
+  }
+};
+
+// ---------------------------------------------------------------- CTA-level transform
+__device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
+
+// One in-place Stockham pass of radix R over nb transforms of length n stored at
+// buf + b * bs + sidx(i).  Requires (n / R) * nb <= MAXB * blockDim.x.
+template <int R, bool INV, int MAXB>
+__device__ __noinline__ void fft_pass(float2* buf, int bs, int n, int nb, int Ns,
+                                         const float2* __restrict__ tw) {
+  const int m = n / R;
+  const int nbf = m * nb;
+  const int twstride = n / (Ns * R);
+  float2 v[MAXB][R];
+#pragma unroll
+  for (int it = 0; it < MAXB; ++it) {
+    const int t = threadIdx.x + it * blockDim.x;
+    if (t < nbf) {
+      const int b = t / m, j = t - b * m;
+      const int k = j % Ns;
+      float2* base = buf + b * bs;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[it][r] = base[sidx(j + r * m)];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = __ldg(&tw[r * k * twstride]);
+          if (INV) w.y = -w.y;
+          v[it][r] = cmul(v[it][r], w);
+        }
+      }
+      DFT<R, INV>::run(v[it]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < MAXB; ++it) {
+    const int t = threadIdx.x + it * blockDim.x;
+    if (t < nbf) {
+      const int b = t / m, j = t - b * m;
+      const int k = j % Ns;
+      const int o = (j - k) * R + k;
+      float2* base = buf + b * bs;
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[sidx(o + r * Ns)] = v[it][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full transform (unnormalised; INV selects exp(+2 pi i k n / N)).  The caller must
+// __syncthreads() after filling buf; the transform ends with a barrier.
+template <bool INV, int MAXB>
+__device__ __forceinline__ void block_fft(float2* buf, int bs, int nb, const FFTDesc& d) {
+  int Ns = 1;
+  for (int p = 0; p < d.npass; ++p) {
+    const int R = d.radix[p];
+    switch (R) {
+      case 2: fft_pass<2, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 3: fft_pass<3, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 4: fft_pass<4, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 5: fft_pass<5, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 6: fft_pass<6, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 8: fft_pass<8, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 9: fft_pass<9, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 10: fft_pass<10, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 12: fft_pass<12, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 15: fft_pass<15, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 16: fft_pass<16, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 20: fft_pass<20, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      case 24: fft_pass<24, INV, MAXB>(buf, bs, d.n, nb, Ns, d.tw); break;
+      default: break;  // the host only builds plans from the radices above
+    }
+    Ns *= R;
+  }
+}
+
+
+}  // namespace cgh

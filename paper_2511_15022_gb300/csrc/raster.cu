@@ -1,0 +1,526 @@
+// raster.cu -- tile-binned complex 2D Gaussian rasteriser, forward and backward (sm_103a).
+//
+// Algorithm 2 of the paper, re-planned for GB300:
+//   1. k_preprocess   one thread per Gaussian: activations (Suppl. activation formulas),
+//                     covariance and its clamped adjugate inverse (Suppl. 2D covariance /
+//                     inversion), per-channel A_c = c cos(phi), B_c = c sin(phi) (hoisted out
+//                     of the pixel loop), and the axis-aligned box of the ellipse where
+//                     alpha G >= cutoff.  Counts the Gaussian in every 16x16 tile its box
+//                     touches.
+//   2. k_scan_tiles   exclusive scan of the per-tile counts (one CTA).
+//   3. k_emit         scatters Gaussian ids into per-tile lists.  The sum over Gaussians is
+//                     order-free, so a counting sort by tile replaces the paper's radix
+//                     sort of (tile, depth) keys.
+//   4. k_raster_fwd   one CTA per tile, one thread per pixel; the tile's Gaussians are
+//                     staged in shared memory 256 at a time; each warp owns an 8x4 pixel
+//                     block and skips (warp-uniformly) Gaussians whose box misses it.
+//   5. k_raster_bwd   same traversal; per-pair gradient terms are reduced across the warp
+//                     with shuffles, accumulated per staged Gaussian with shared-memory
+//                     atomics, and flushed once per tile with global atomics.
+//   6. k_grad_finalize one thread per Gaussian: chain rule from the accumulated moments to
+//                     the pre-activation parameters (Suppl. items 1-7; the
+//                     inverse-covariance -> covariance step is the exact derivative of the
+//                     adjugate formula, which the paper does not print).
+// If the (Gaussian, tile) list outgrows its capacity, tiles past the capacity evaluate
+// every Gaussian with the same box test instead: slower, still exact.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "cgh_internal.h"
+
+namespace cgh {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kP2Floor = -50.0f * 1.4426950408889634f;  // power clamp -50 in log2 units
+constexpr float kAlphaCap = 0.99f;
+
+struct RasterConsts {
+  int H, W, C, N, tiles_x, tiles_y;
+  float cutoff;
+  int _pad;
+  long long cap;
+};
+
+__device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
+
+// Activated quantities of one Gaussian (shared by preprocess and finalize).
+struct Act {
+  float tx, ty, mx, my, esx, esy, sx, sy, c, s, S00, S01, S11, det, i00, i01, i11, alpha;
+};
+
+__device__ __forceinline__ Act activate(const cgh_params& p, int n, int W, int H) {
+  Act a;
+  a.tx = tanhf(p.xy_raw[2 * n + 0]);
+  a.ty = tanhf(p.xy_raw[2 * n + 1]);
+  a.mx = (a.tx + 1.0f) * 0.5f * (float)W;
+  a.my = (a.ty + 1.0f) * 0.5f * (float)H;
+  a.esx = expf(p.s_raw[2 * n + 0]);
+  a.esy = expf(p.s_raw[2 * n + 1]);
+  a.sx = a.esx + 0.1f;
+  a.sy = a.esy + 0.1f;
+  sincosf(p.theta[n], &a.s, &a.c);
+  float sx2 = a.sx * a.sx, sy2 = a.sy * a.sy;
+  a.S00 = sx2 * a.c * a.c + sy2 * a.s * a.s + 0.1f;
+  a.S01 = (sx2 - sy2) * a.c * a.s;
+  a.S11 = sx2 * a.s * a.s + sy2 * a.c * a.c + 0.1f;
+  a.det = a.S00 * a.S11 - a.S01 * a.S01;
+  float ds = fmaxf(a.det, 1e-10f);
+  a.i00 = a.S11 / ds;
+  a.i01 = -a.S01 / ds;
+  a.i11 = a.S00 / ds;
+  a.alpha = 1.0f / (1.0f + expf(-p.alpha_raw[n]));
+  return a;
+}
+
+__global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__ rec,
+                             int4* __restrict__ rect, int* __restrict__ tile_count,
+                             int* __restrict__ status) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= rc.N) return;
+  const int C = rc.C;
+  bool ok = finitef(p.xy_raw[2 * n]) && finitef(p.xy_raw[2 * n + 1]) &&
+            finitef(p.s_raw[2 * n]) && finitef(p.s_raw[2 * n + 1]) && finitef(p.theta[n]) &&
+            finitef(p.alpha_raw[n]);
+  float A[CGH_MAX_C] = {0.f, 0.f, 0.f, 0.f}, B[CGH_MAX_C] = {0.f, 0.f, 0.f, 0.f};
+  for (int c = 0; c < C; ++c) {
+    float amp = p.amp[n * C + c], ph = p.phase[n * C + c];
+    ok = ok && finitef(amp) && finitef(ph);
+    float sp, cp;
+    sincosf(ph, &sp, &cp);
+    A[c] = amp * cp;
+    B[c] = amp * sp;
+  }
+  if (!ok) atomicExch(&status[ST_NONFINITE], 1);
+  Act a = activate(p, n, rc.W, rc.H);
+  const float k = -0.5f * kLog2e;
+  float thr = rc.cutoff > 0.f ? log2f(rc.cutoff / a.alpha) : -INFINITY;
+  // box of the ellipse m <= m*, m* = 2 ln(alpha / cutoff) (power floor m = 100 in smooth
+  // mode); half-widths sqrt(m* S00), sqrt(m* S11), widened slightly for FP32 rounding.
+  float mstar = rc.cutoff > 0.f ? 2.0f * logf(a.alpha / rc.cutoff) : 100.0f;
+  int4 r = make_int4(1, 1, 0, 0);  // empty
+  float bx0 = 1.f, bx1 = 0.f, by0 = 1.f, by1 = 0.f;
+  if (ok && a.alpha >= rc.cutoff && mstar >= 0.f && isfinite(a.mx) && isfinite(a.my)) {
+    float rx = sqrtf(mstar * a.S00) * 1.0001f + 0.01f;
+    float ry = sqrtf(mstar * a.S11) * 1.0001f + 0.01f;
+    bx0 = fmaxf(a.mx - rx, 0.f);
+    bx1 = fminf(a.mx + rx, (float)(rc.W - 1));
+    by0 = fmaxf(a.my - ry, 0.f);
+    by1 = fminf(a.my + ry, (float)(rc.H - 1));
+    if (bx0 <= bx1 && by0 <= by1 && isfinite(rx) && isfinite(ry)) {
+      r.x = (int)floorf(bx0) / CGH_TILE;
+      r.z = (int)floorf(bx1) / CGH_TILE;
+      r.y = (int)floorf(by0) / CGH_TILE;
+      r.w = (int)floorf(by1) / CGH_TILE;
+    } else {
+      bx0 = 1.f; bx1 = 0.f; by0 = 1.f; by1 = 0.f;
+    }
+  }
+  float4* o = rec + (size_t)n * CGH_REC_F4;
+  o[0] = make_float4(a.mx, a.my, k * a.i00, 2.0f * k * a.i01);
+  o[1] = make_float4(k * a.i11, thr, a.alpha, 0.f);
+  o[2] = make_float4(bx0, bx1, by0, by1);
+  o[3] = make_float4(A[0], B[0], A[1], B[1]);
+  o[4] = make_float4(A[2], B[2], A[3], B[3]);
+  rect[n] = r;
+  for (int ty = r.y; ty <= r.w; ++ty)
+    for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&tile_count[ty * rc.tiles_x + tx], 1);
+}
+
+// Exclusive scan of tile counts (one CTA of 1024 threads).  tile_start has T+1 entries;
+// tile_count is reset to zero so that k_emit can use it as the per-tile cursor.
+__global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
+                                                     int* __restrict__ tile_count,
+                                                     int* __restrict__ tile_start,
+                                                     int* __restrict__ status) {
+  __shared__ long long warp_sums[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int per = (T + nt - 1) / nt;
+  const int beg = min(T, tid * per), end = min(T, beg + per);
+  long long local = 0;
+  for (int i = beg; i < end; ++i) local += tile_count[i];
+  // inclusive scan of `local` over the CTA
+  long long v = local;
+  const int lane = tid & 31, wid = tid >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = (lane < (nt >> 5)) ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    warp_sums[lane] = w;
+  }
+  __syncthreads();
+  long long excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+  for (int i = beg; i < end; ++i) {
+    int cnt = tile_count[i];
+    tile_start[i] = (int)min(excl, (long long)0x7fffffff);
+    excl += cnt;
+    tile_count[i] = 0;
+  }
+  if (tid == nt - 1) {
+    tile_start[T] = (int)min(excl, (long long)0x7fffffff);
+    status[ST_PAIRS_LO] = (int)(excl & 0xffffffff);
+    status[ST_PAIRS_HI] = (int)(excl >> 32);
+    if (excl > cap) status[ST_OVERFLOW] = 1;
+  }
+}
+
+__global__ void k_emit(RasterConsts rc, const int4* __restrict__ rect,
+                       const int* __restrict__ tile_start, int* __restrict__ cursor,
+                       int* __restrict__ pairs) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= rc.N) return;
+  int4 r = rect[n];
+  for (int ty = r.y; ty <= r.w; ++ty)
+    for (int tx = r.x; tx <= r.z; ++tx) {
+      int t = ty * rc.tiles_x + tx;
+      long long pos = (long long)tile_start[t] + atomicAdd(&cursor[t], 1);
+      if (pos < rc.cap) pairs[pos] = n;
+    }
+}
+
+// Stage records [base, base + 256) of a tile's list into shared memory.  In exhaustive
+// mode (list overflowed) the candidates are all Gaussians and the ones whose tile
+// rectangle misses this tile get an empty box.
+__device__ __forceinline__ int stage_batch(const RasterConsts& rc, const float4* __restrict__ rec,
+                                           const int4* __restrict__ rect,
+                                           const int* __restrict__ pairs, int start, int count,
+                                           bool exhaustive, int base, int tx, int ty,
+                                           float4* srec, int* sgid) {
+  const int i = base + threadIdx.x;
+  if (i < count) {
+    int gid = exhaustive ? i : pairs[start + i];
+    const float4* g = rec + (size_t)gid * CGH_REC_F4;
+#pragma unroll
+    for (int k = 0; k < CGH_REC_F4; ++k) srec[threadIdx.x * CGH_REC_F4 + k] = g[k];
+    if (exhaustive) {
+      int4 r = rect[gid];
+      if (tx < r.x || tx > r.z || ty < r.y || ty > r.w)
+        srec[threadIdx.x * CGH_REC_F4 + 2] = make_float4(1.f, 0.f, 1.f, 0.f);
+    }
+    if (sgid) sgid[threadIdx.x] = gid;
+  }
+  return min(256, count - base);
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float4* __restrict__ rec,
+                                                    const int4* __restrict__ rect,
+                                                    const int* __restrict__ tile_start,
+                                                    const int* __restrict__ pairs,
+                                                    float2* __restrict__ U) {
+  __shared__ float4 srec[256 * CGH_REC_F4];
+  const int tx = blockIdx.x, ty = blockIdx.y;
+  const int tile = ty * rc.tiles_x + tx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wx0 = tx * CGH_TILE + (warp & 1) * 8, wy0 = ty * CGH_TILE + (warp >> 1) * 4;
+  const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
+  const float fpx = (float)px, fpy = (float)py;
+  const float fwx0 = (float)wx0, fwx1 = (float)(wx0 + 7), fwy0 = (float)wy0,
+              fwy1 = (float)(wy0 + 3);
+  const int start = tile_start[tile], end = tile_start[tile + 1];
+  const bool exhaustive = (long long)end > rc.cap;
+  const int count = exhaustive ? rc.N : end - start;
+  float accr[C], acci[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) { accr[c] = 0.f; acci[c] = 0.f; }
+  for (int base = 0; base < count; base += 256) {
+    __syncthreads();
+    const int nb = stage_batch(rc, rec, rect, pairs, start, count, exhaustive, base, tx, ty,
+                               srec, nullptr);
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const float4 bb = srec[j * CGH_REC_F4 + 2];
+      if (bb.y < fwx0 || bb.x > fwx1 || bb.w < fwy0 || bb.z > fwy1) continue;  // warp-uniform
+      const float4 r0 = srec[j * CGH_REC_F4 + 0];
+      const float4 r1 = srec[j * CGH_REC_F4 + 1];
+      const float dx = fpx - r0.x, dy = fpy - r0.y;
+      const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
+      if (p2 >= r1.y) {
+        const float G = exp2f(fmaxf(p2, kP2Floor));
+        const float a = fminf(kAlphaCap, r1.z * G);
+        const float4 r3 = srec[j * CGH_REC_F4 + 3];
+        const float4 r4 = srec[j * CGH_REC_F4 + 4];
+        const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+        const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          accr[c] = fmaf(a, Ac[c], accr[c]);
+          acci[c] = fmaf(a, Bc[c], acci[c]);
+        }
+      }
+    }
+  }
+  if (px < rc.W && py < rc.H) {
+    const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
+#pragma unroll
+    for (int c = 0; c < C; ++c) U[c * plane + o] = make_float2(accr[c], acci[c]);
+  }
+}
+
+// Raw accumulated moments per Gaussian (NV = 2C + 6 values):
+//   [0, C)      P_c = sum a dL/dRe_c          [C, 2C)  Q_c = sum a dL/dIm_c
+//   2C          SG  = sum G S (unclamped pairs), S = sum_c (A_c dRe_c + B_c dIm_c)
+//   2C+1..2C+5  sum u dx, u dy, u dx^2, u dx dy, u dy^2 with u = S alpha G (power unclamped)
+template <int C>
+__global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float4* __restrict__ rec,
+                                                    const int4* __restrict__ rect,
+                                                    const int* __restrict__ tile_start,
+                                                    const int* __restrict__ pairs,
+                                                    const float2* __restrict__ dU,
+                                                    float* __restrict__ raw) {
+  constexpr int NV = 2 * C + 6;
+  __shared__ float4 srec[256 * CGH_REC_F4];
+  __shared__ float sacc[256 * NV];
+  __shared__ int sgid[256];
+  const int tx = blockIdx.x, ty = blockIdx.y;
+  const int tile = ty * rc.tiles_x + tx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wx0 = tx * CGH_TILE + (warp & 1) * 8, wy0 = ty * CGH_TILE + (warp >> 1) * 4;
+  const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
+  const float fpx = (float)px, fpy = (float)py;
+  const float fwx0 = (float)wx0, fwx1 = (float)(wx0 + 7), fwy0 = (float)wy0,
+              fwy1 = (float)(wy0 + 3);
+  const bool inside = px < rc.W && py < rc.H;
+  float gR[C], gI[C];
+  {
+    const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float2 g = inside ? dU[c * plane + o] : make_float2(0.f, 0.f);
+      gR[c] = g.x;
+      gI[c] = g.y;
+    }
+  }
+  const int start = tile_start[tile], end = tile_start[tile + 1];
+  const bool exhaustive = (long long)end > rc.cap;
+  const int count = exhaustive ? rc.N : end - start;
+  for (int base = 0; base < count; base += 256) {
+    __syncthreads();
+    const int nb = stage_batch(rc, rec, rect, pairs, start, count, exhaustive, base, tx, ty,
+                               srec, sgid);
+    for (int t = threadIdx.x; t < 256 * NV; t += 256) sacc[t] = 0.f;
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+      const float4 bb = srec[j * CGH_REC_F4 + 2];
+      if (bb.y < fwx0 || bb.x > fwx1 || bb.w < fwy0 || bb.z > fwy1) continue;  // warp-uniform
+      const float4 r0 = srec[j * CGH_REC_F4 + 0];
+      const float4 r1 = srec[j * CGH_REC_F4 + 1];
+      const float dx = fpx - r0.x, dy = fpy - r0.y;
+      const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
+      const bool pass = inside && p2 >= r1.y;
+      if (!__any_sync(0xffffffffu, pass)) continue;
+      float val[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) val[v] = 0.f;
+      if (pass) {
+        const float4 r3 = srec[j * CGH_REC_F4 + 3];
+        const float4 r4 = srec[j * CGH_REC_F4 + 4];
+        const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+        const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+        const float G = exp2f(fmaxf(p2, kP2Floor));
+        const float aG = r1.z * G;
+        const float a = fminf(kAlphaCap, aG);
+        float S = 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          val[c] = a * gR[c];
+          val[C + c] = a * gI[c];
+          S = fmaf(Ac[c], gR[c], fmaf(Bc[c], gI[c], S));
+        }
+        if (aG < kAlphaCap) {
+          val[2 * C] = S * G;
+          if (p2 > kP2Floor) {
+            const float u = S * aG;
+            const float udx = u * dx, udy = u * dy;
+            val[2 * C + 1] = udx;
+            val[2 * C + 2] = udy;
+            val[2 * C + 3] = udx * dx;
+            val[2 * C + 4] = udx * dy;
+            val[2 * C + 5] = udy * dy;
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val[v] += __shfl_xor_sync(0xffffffffu, val[v], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) atomicAdd(&sacc[j * NV + v], val[v]);
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb * NV; t += 256) {
+      const float v = sacc[t];
+      if (v != 0.f) atomicAdd(&raw[(size_t)sgid[t / NV] * CGH_RAW_STRIDE + (t % NV)], v);
+    }
+  }
+}
+
+template <int C>
+__global__ void k_grad_finalize(RasterConsts rc, cgh_params p, const float* __restrict__ raw,
+                                cgh_grads g) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= rc.N) return;
+  const float* r = raw + (size_t)n * CGH_RAW_STRIDE;
+  bool ok = finitef(p.xy_raw[2 * n]) && finitef(p.xy_raw[2 * n + 1]) &&
+            finitef(p.s_raw[2 * n]) && finitef(p.s_raw[2 * n + 1]) && finitef(p.theta[n]) &&
+            finitef(p.alpha_raw[n]);
+  for (int c = 0; c < C; ++c) ok = ok && finitef(p.amp[n * C + c]) && finitef(p.phase[n * C + c]);
+  if (!ok) {
+    g.xy_raw[2 * n] = 0.f; g.xy_raw[2 * n + 1] = 0.f; g.s_raw[2 * n] = 0.f;
+    g.s_raw[2 * n + 1] = 0.f; g.theta[n] = 0.f; g.alpha_raw[n] = 0.f;
+    for (int c = 0; c < C; ++c) { g.amp[n * C + c] = 0.f; g.phase[n * C + c] = 0.f; }
+    return;
+  }
+  Act a = activate(p, n, rc.W, rc.H);
+  // items 1, 2: amplitude and phase
+  for (int c = 0; c < C; ++c) {
+    float sp, cp;
+    sincosf(p.phase[n * C + c], &sp, &cp);
+    const float P = r[c], Q = r[C + c];
+    g.amp[n * C + c] = cp * P + sp * Q;
+    g.phase[n * C + c] = p.amp[n * C + c] * (cp * Q - sp * P);
+  }
+  // item 3: opacity through the sigmoid
+  g.alpha_raw[n] = r[2 * C] * a.alpha * (1.f - a.alpha);
+  // item 4: mean, dL/dx = inv . sum(u d), then tanh: W/2 (1 - tanh^2)
+  const float Sx = r[2 * C + 1], Sy = r[2 * C + 2];
+  const float dmx = a.i00 * Sx + a.i01 * Sy;
+  const float dmy = a.i01 * Sx + a.i11 * Sy;
+  g.xy_raw[2 * n + 0] = dmx * 0.5f * (float)rc.W * (1.f - a.tx * a.tx);
+  g.xy_raw[2 * n + 1] = dmy * 0.5f * (float)rc.H * (1.f - a.ty * a.ty);
+  // item 5: inverse covariance, dL/dinv = -1/2 sum u (dx^2, 2 dx dy, dy^2)
+  const float d00 = -0.5f * r[2 * C + 3], d01 = -r[2 * C + 4], d11 = -0.5f * r[2 * C + 5];
+  // inverse -> covariance: inv = (S11, -S01, S00) / D, D = S00 S11 - S01^2
+  float dS00, dS01, dS11;
+  const float A_ = a.S00, B_ = a.S01, C_ = a.S11;
+  if (a.det > 1e-10f) {
+    const float iD2 = 1.f / (a.det * a.det);
+    dS00 = (-C_ * C_ * d00 + B_ * C_ * d01 - B_ * B_ * d11) * iD2;
+    dS01 = (2.f * B_ * C_ * d00 - (A_ * C_ + B_ * B_) * d01 + 2.f * A_ * B_ * d11) * iD2;
+    dS11 = (-B_ * B_ * d00 + A_ * B_ * d01 - A_ * A_ * d11) * iD2;
+  } else {
+    dS00 = d11 / 1e-10f;
+    dS01 = -d01 / 1e-10f;
+    dS11 = d00 / 1e-10f;
+  }
+  // items 6, 7: scales (then exp) and rotation
+  const float cc = a.c * a.c, ss = a.s * a.s, cs = a.c * a.s;
+  const float sx2 = a.sx * a.sx, sy2 = a.sy * a.sy;
+  const float dsx = 2.f * a.sx * (cc * dS00 + cs * dS01 + ss * dS11);
+  const float dsy = 2.f * a.sy * (ss * dS00 - cs * dS01 + cc * dS11);
+  g.s_raw[2 * n + 0] = dsx * a.esx;
+  g.s_raw[2 * n + 1] = dsy * a.esy;
+  g.theta[n] = 2.f * (sy2 - sx2) * cs * dS00 + (sx2 - sy2) * (cc - ss) * dS01 +
+               2.f * (sx2 - sy2) * cs * dS11;
+}
+
+}  // namespace cgh
+
+using namespace cgh;
+
+static RasterConsts make_consts(const cgh_plan* p, int N) {
+  RasterConsts rc;
+  rc.H = p->H; rc.W = p->W; rc.C = p->C; rc.N = N;
+  rc.tiles_x = p->tiles_x; rc.tiles_y = p->tiles_y;
+  rc.cutoff = p->cutoff; rc._pad = 0;
+  rc.cap = p->pair_capacity;
+  return rc;
+}
+
+// Binning shared by forward and backward: preprocess, scan, emit.
+static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
+  const int T = p->tiles_x * p->tiles_y;
+  RasterConsts rc = make_consts(p, prm->N);
+  int* tile_count = (int*)(p->ws + p->off_tile_count);
+  int* tile_start = (int*)(p->ws + p->off_tile_start);
+  int* status = (int*)(p->ws + p->off_status);
+  cudaError_t e = cudaMemsetAsync(tile_count, 0, sizeof(int) * T, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(status, 0, sizeof(int) * ST_COUNT, s);
+  if (e != cudaSuccess) return e;
+  const int nblk = (prm->N + 255) / 256;
+  if (prm->N > 0) {
+    prof_begin(KID_PREPROCESS, s);
+    k_preprocess<<<nblk, 256, 0, s>>>(rc, *prm, (float4*)(p->ws + p->off_rec),
+                                      (int4*)(p->ws + p->off_rect), tile_count, status);
+    prof_end(KID_PREPROCESS, s);
+  }
+  prof_begin(KID_SCAN_TILES, s);
+  k_scan_tiles<<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  prof_end(KID_SCAN_TILES, s);
+  if (prm->N > 0) {
+    prof_begin(KID_EMIT, s);
+    k_emit<<<nblk, 256, 0, s>>>(rc, (const int4*)(p->ws + p->off_rect), tile_start, tile_count,
+                                (int*)(p->ws + p->off_pairs));
+    prof_end(KID_EMIT, s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s) {
+  cudaError_t e = bin(p, prm, s);
+  if (e != cudaSuccess) return e;
+  RasterConsts rc = make_consts(p, prm->N);
+  dim3 grid(p->tiles_x, p->tiles_y);
+  const float4* rec = (const float4*)(p->ws + p->off_rec);
+  const int4* rect = (const int4*)(p->ws + p->off_rect);
+  const int* ts = (const int*)(p->ws + p->off_tile_start);
+  const int* pairs = (const int*)(p->ws + p->off_pairs);
+  prof_begin(KID_RASTER_FWD, s);
+  switch (p->C) {
+    case 1: k_raster_fwd<1><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
+    case 2: k_raster_fwd<2><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
+    case 3: k_raster_fwd<3><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
+    default: k_raster_fwd<4><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
+  }
+  prof_end(KID_RASTER_FWD, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* dU,
+                              const cgh_grads* g, cudaStream_t s, bool rebin) {
+  cudaError_t e = rebin ? bin(p, prm, s) : cudaSuccess;
+  if (e != cudaSuccess) return e;
+  float* raw = (float*)(p->ws + p->off_raw);
+  if (prm->N > 0) {
+    e = cudaMemsetAsync(raw, 0, sizeof(float) * CGH_RAW_STRIDE * (size_t)prm->N, s);
+    if (e != cudaSuccess) return e;
+  }
+  RasterConsts rc = make_consts(p, prm->N);
+  dim3 grid(p->tiles_x, p->tiles_y);
+  const float4* rec = (const float4*)(p->ws + p->off_rec);
+  const int4* rect = (const int4*)(p->ws + p->off_rect);
+  const int* ts = (const int*)(p->ws + p->off_tile_start);
+  const int* pairs = (const int*)(p->ws + p->off_pairs);
+  const int nblk = (prm->N + 255) / 256;
+  prof_begin(KID_RASTER_BWD, s);
+  switch (p->C) {
+    case 1: k_raster_bwd<1><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    case 2: k_raster_bwd<2><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    case 3: k_raster_bwd<3><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    default: k_raster_bwd<4><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+  }
+  prof_end(KID_RASTER_BWD, s);
+  if (prm->N > 0) {
+    prof_begin(KID_GRAD_FINALIZE, s);
+    switch (p->C) {
+      case 1: k_grad_finalize<1><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
+      case 2: k_grad_finalize<2><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
+      case 3: k_grad_finalize<3><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
+      default: k_grad_finalize<4><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
+    }
+    prof_end(KID_GRAD_FINALIZE, s);
+  }
+  return cudaGetLastError();
+}
