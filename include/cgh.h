@@ -107,12 +107,15 @@ cgh_status cgh_plan_set_workspace(cgh_plan* plan, void* workspace, size_t bytes)
  *   col_block    columns per CTA in the column FFT passes (1, 2, 4 or 8)
  *   row_block    rows per CTA in the row FFT passes (1..8)
  *   fft_threads  threads per CTA of the FFT passes (128..1024)
- *   pair_capacity_per_gaussian  (Gaussian, tile) list capacity as a multiple of N */
+ *   pair_capacity_per_gaussian  (Gaussian, tile) list capacity as a multiple of N
+ *   fft_kernels  1: compile-time specialised FFT kernels where one matches the padded
+ *                length and block shape (default), 2: generic mixed-radix kernels only */
 typedef struct {
   int32_t col_block;
   int32_t row_block;
   int32_t fft_threads;
   int32_t pair_capacity_per_gaussian;
+  int32_t fft_kernels;
 } cgh_tuning;
 
 cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* tuning);

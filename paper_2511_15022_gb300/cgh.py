@@ -33,7 +33,8 @@ class _Grads(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("col_block", ctypes.c_int32), ("row_block", ctypes.c_int32),
-                ("fft_threads", ctypes.c_int32), ("pair_capacity_per_gaussian", ctypes.c_int32)]
+                ("fft_threads", ctypes.c_int32), ("pair_capacity_per_gaussian", ctypes.c_int32),
+                ("fft_kernels", ctypes.c_int32)]
 
 
 class _AdamGroup(ctypes.Structure):
@@ -186,8 +187,9 @@ class Plan:
         _check(_lib.cgh_plan_workspace_bytes(self._h, ctypes.byref(n)), "workspace_bytes")
         return int(n.value)
 
-    def set_tuning(self, col_block=0, row_block=0, fft_threads=0, pair_capacity_per_gaussian=0):
-        t = _Tuning(col_block, row_block, fft_threads, pair_capacity_per_gaussian)
+    def set_tuning(self, col_block=0, row_block=0, fft_threads=0, pair_capacity_per_gaussian=0,
+                   fft_kernels=0):
+        t = _Tuning(col_block, row_block, fft_threads, pair_capacity_per_gaussian, fft_kernels)
         _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
         if self._ws is not None:
             self._attach_workspace()

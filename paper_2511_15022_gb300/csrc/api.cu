@@ -10,6 +10,7 @@
 
 #include <new>
 
+#include "blasm_spec.h"
 #include "cgh_internal.h"
 
 static thread_local char g_err[512] = "";
@@ -203,6 +204,25 @@ extern "C" cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L
   p->tables_bytes = tbytes;
   p->fx.tw = (const float2*)p->tables_dev;
   p->fy.tw = (const float2*)p->tables_dev + Nx;
+  // prefer block shapes with compile-time specialised kernels
+  p->use_spec = 1;
+  {
+    static const int cbs[] = {4, 2, 8, 1};
+    static const int rbs[] = {4, 2, 1, 8};
+    bool done = false;
+    for (int cb : cbs) {
+      if (done || Nx % cb || !spec_cols(0, (int)Ny, cb, nullptr, nullptr, nullptr, 0, nullptr, true))
+        continue;
+      for (int rb : rbs) {
+        if (spec_rows(0, (int)Nx, rb, cb, nullptr, nullptr, 0, nullptr, true)) {
+          p->col_block = cb;
+          p->row_block = rb;
+          done = true;
+          break;
+        }
+      }
+    }
+  }
   // largest column / row blocks (<= 4 / 2) whose transforms fit one CTA
   while (p->col_block > 1 && !fft_shape(p, p->fy, p->col_block, 2).ok) p->col_block /= 2;
   while (p->row_block > 1 && !fft_shape(p, p->fx, p->row_block, 1).ok) p->row_block /= 2;
@@ -262,6 +282,10 @@ extern "C" cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* t) {
       return fail(CGH_ERR_ARG, "fft_threads must be a multiple of 32 in 64..%d", kMaxFFTThreads);
     plan->fft_threads = t->fft_threads;
   }
+  if (t->fft_kernels) {
+    if (t->fft_kernels != 1 && t->fft_kernels != 2) return fail(CGH_ERR_ARG, "fft_kernels must be 1 or 2");
+    plan->use_spec = t->fft_kernels == 1;
+  }
   if (t->pair_capacity_per_gaussian) {
     if (t->pair_capacity_per_gaussian < 1) return fail(CGH_ERR_ARG, "pair capacity must be >= 1");
     plan->pair_cap_mult = t->pair_capacity_per_gaussian;
@@ -282,6 +306,7 @@ extern "C" cgh_status cgh_plan_get_tuning(const cgh_plan* plan, cgh_tuning* out)
   out->row_block = plan->row_block;
   out->fft_threads = plan->fft_threads;
   out->pair_capacity_per_gaussian = plan->pair_cap_mult;
+  out->fft_kernels = plan->use_spec ? 1 : 2;
   return CGH_OK;
 }
 

@@ -23,36 +23,10 @@
 
 #include "cgh_internal.h"
 #include "fft.cuh"
+#include "blasm_common.cuh"
+#include "blasm_spec.h"
 
 namespace cgh {
-
-__device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
-
-// H_{c,l}(s_x, s_y) * scale, Algorithm 3.  Phase k_z d / 2 pi is evaluated as
-// frac(d / lambda) - (d/lambda) q / (1 + sqrt(1 - q)) with q = lambda^2 (f_x^2 + f_y^2)
-// (the same value as (d / lambda) sqrt(1 - q); the large integer number of turns is removed
-// on the host in FP64).  Evanescent bins inside the band get k_z = 0 (H = 1).
-__device__ __forceinline__ float2 transfer(const BlasmDev& bl, int cl, int sx, int sy,
-                                           float scale) {
-  const TFConst& t = bl.tf[cl];
-  if (abs(sx) > t.kx_max || abs(sy) > t.ky_max) return make_float2(0.f, 0.f);
-  if (bl.aperture2 > 0.f) {
-    const float ax = (float)sx + 0.5f, ay = (float)sy + 0.5f;
-    if (ax * ax + ay * ay >= bl.aperture2) return make_float2(0.f, 0.f);
-  }
-  const float fx2 = (float)(sx * sx), fy2 = (float)(sy * sy);
-  const float q = fmaf(t.qx, fx2, t.qy * fy2);
-  float turns = 0.f;
-  if (q < 1.f) {
-    const float den = 1.f + sqrtf(1.f - q);
-    const float num = fmaf(t.ax, fx2, t.ay * fy2);
-    turns = t.turns0 - num / den;
-    turns -= rintf(turns);
-  }
-  float s, c;
-  sincospif(2.f * turns, &s, &c);
-  return make_float2(c * scale, s * scale);
-}
 
 template <int MAXB>
 __global__ void __launch_bounds__(512, 1) k_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
@@ -142,20 +116,6 @@ __global__ void __launch_bounds__(512, 1) k_rows_inv_crop(const __grid_constant_
     const int b = idx / W, x = idx - b * W;
     dst[(size_t)(y0 + b) * W + x] = sm[b * bs + sidx(bl.ox + x)];
   }
-}
-
-__device__ __forceinline__ float block_sum(float v, float* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  float t = 0.f;
-  if (threadIdx.x < 32) {
-    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  }
-  return t;  // valid in thread 0
 }
 
 template <int MAXB>
@@ -352,8 +312,37 @@ int pointwise_loss_blocks(const cgh_plan* p) {
   return 592;  // 4 blocks of 256 threads per SM on a 148-152 SM part
 }
 
+bool spec_rows(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRowArgs* a,
+               cudaStream_t s, cudaError_t* err, bool dry) {
+  return spec_rows_a(kind, N, RB, CB, p, a, s, err, dry) ||
+         spec_rows_b(kind, N, RB, CB, p, a, s, err, dry);
+}
+
+bool spec_cols(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
+               cudaStream_t s, cudaError_t* err, bool dry) {
+  return spec_cols_a(kind, N, CB, p, in, out, s, err, dry) ||
+         spec_cols_b(kind, N, CB, p, in, out, s, err, dry);
+}
+
+static bool try_spec_rows(int kind, cgh_plan* p, const SpecRowArgs& a, cudaStream_t s,
+                          cudaError_t* err) {
+  if (!p->use_spec) return false;
+  return spec_rows(kind, p->fx.n, p->row_block, p->col_block, p, &a, s, err, false);
+}
+
+static bool try_spec_cols(int kind, cgh_plan* p, const float2* in, float2* out, cudaStream_t s,
+                          cudaError_t* err) {
+  if (!p->use_spec) return false;
+  return spec_cols(kind, p->fy.n, p->col_block, p, in, out, s, err, false);
+}
+
 cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,
                                 cudaStream_t s) {
+  {
+    cudaError_t e;
+    SpecRowArgs a{in, half, nullptr, nullptr, batches, 0};
+    if (try_spec_rows(SPEC_ROWS_PAD_FWD, p, a, s, &e)) return e;
+  }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
   LaunchShape sh = fft_shape(p, p->fx, RB, 1);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
@@ -365,6 +354,10 @@ cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int
 }
 
 cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s) {
+  {
+    cudaError_t e;
+    if (try_spec_cols(SPEC_COLS_FWD_PLANES, p, Y, V, s, &e)) return e;
+  }
   const int CB = p->col_block, bs = smem_stride(p->fy.n);
   LaunchShape sh = fft_shape(p, p->fy, CB, 2);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
@@ -377,6 +370,11 @@ cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cuda
 
 cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, int batches,
                                  cudaStream_t s) {
+  {
+    cudaError_t e;
+    SpecRowArgs a{half, out, nullptr, nullptr, batches, 0};
+    if (try_spec_rows(SPEC_ROWS_INV_CROP, p, a, s, &e)) return e;
+  }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
   LaunchShape sh = fft_shape(p, p->fx, RB, 1);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
@@ -389,6 +387,11 @@ cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, i
 
 cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
                              cudaStream_t s, bool want_grad) {
+  {
+    cudaError_t e;
+    SpecRowArgs a{nullptr, V, target, partials, p->L * p->C, want_grad ? 1 : 0};
+    if (try_spec_rows(SPEC_ROWS_LOSS, p, a, s, &e)) return e;
+  }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
   LaunchShape sh = fft_shape(p, p->fx, RB, 1);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
@@ -400,6 +403,10 @@ cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float*
 }
 
 cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s) {
+  {
+    cudaError_t e;
+    if (try_spec_cols(SPEC_COLS_BWD_PLANES, p, G, D, s, &e)) return e;
+  }
   const int CB = p->col_block, bs = smem_stride(p->fy.n);
   LaunchShape sh = fft_shape(p, p->fy, CB, 2);
   if (!sh.ok) return cudaErrorInvalidConfiguration;

@@ -1,0 +1,304 @@
+// blasm_reg.cuh -- BLASM row / column passes on the specialised register FFT engine.
+//
+// Same passes and data layouts as the generic kernels of blasm.cu (see there), with
+// every transform length a template constant:
+//   kr_rows_pad_fwd    global rows (zero-skipped pad) -> FFT -> blocked half grid
+//   kr_cols_fwd_planes column slab -> FFT -> spectrum in registers -> for each plane
+//                      x H_{c,l}/(Ny Nx) -> inverse FFT -> cropped rows
+//   kr_rows_loss       inverse row FFT -> crop, |U|^2, loss partials, dL/dU seed in
+//                      registers -> forward row FFT -> in place
+//   kr_cols_bwd_planes for each plane: FFT -> x conj(H_{c,l})/(Ny Nx), accumulated in
+//                      registers -> one inverse FFT -> cropped rows
+//   kr_rows_inv_crop   blocked half grid -> inverse FFT -> cropped image rows
+#pragma once
+
+#include "blasm_common.cuh"
+#include "blasm_spec.h"
+#include "fftreg.cuh"
+
+namespace cgh {
+
+template <int N, int R0, int R1, int R2, int NB, int T>
+struct RegPlan {
+  using F = reg::Seq<N, R0, R1, R2, NB, T, false>;
+  using I = reg::Seq<N, R0, R1, R2, NB, T, true>;
+  static constexpr int BUF = reg::BufSize<N, NB, R0, R1, R2>::elems;
+  static constexpr size_t SMEM = sizeof(float2) * (size_t)BUF;
+};
+
+template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+__global__ void __launch_bounds__(T) kr_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
+                                                     const float2* __restrict__ tw,
+                                                     const float2* __restrict__ in,
+                                                     float2* __restrict__ half) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using F = typename P::F;
+  extern __shared__ float2 buf[];
+  const int batch = blockIdx.y, y0 = blockIdx.x * NB;
+  const int H = bl.H, W = bl.W, ox = bl.ox;
+  const float2* src = in + (size_t)batch * H * W;
+  float2 v[F::GA::MB][F::A];
+  reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
+    const int x = a - ox, y = y0 + b;
+    return (x >= 0 && x < W && y < H) ? __ldg(&src[(size_t)y * W + x]) : make_float2(0.f, 0.f);
+  });
+  float2 out[F::GC::MB][F::C];
+  F::rest(v, out, buf, tw);
+  float2* dst = half + (size_t)batch * H * N;
+  reg::for_each<N, F::C, NB, T>(out, [&](int b, int a, float2& val) {
+    const int y = y0 + b;
+    if (y < H) dst[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
+  });
+}
+
+template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+__global__ void __launch_bounds__(T) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
+                                                      const float2* __restrict__ tw,
+                                                      const float2* __restrict__ half,
+                                                      float2* __restrict__ out) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using I = typename P::I;
+  extern __shared__ float2 buf[];
+  const int batch = blockIdx.y, y0 = blockIdx.x * NB;
+  const int H = bl.H, W = bl.W, ox = bl.ox;
+  const float2* src = half + (size_t)batch * H * N;
+  float2 v[I::GA::MB][I::A];
+  reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
+    const int y = y0 + b;
+    return y < H ? __ldg(&src[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
+  });
+  float2 u[I::GC::MB][I::C];
+  I::rest(v, u, buf, tw);
+  float2* dst = out + (size_t)batch * H * W;
+  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+    const int x = a - ox, y = y0 + b;
+    if (x >= 0 && x < W && y < H) dst[(size_t)y * W + x] = val;
+  });
+}
+
+template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+__global__ void __launch_bounds__(T) kr_rows_loss(const __grid_constant__ BlasmDev bl,
+                                                  const float2* __restrict__ tw,
+                                                  float2* __restrict__ V,
+                                                  const float* __restrict__ target,
+                                                  float* __restrict__ partials, int want_grad) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using F = typename P::F;
+  using I = typename P::I;
+  static_assert(I::C == F::A, "inverse must end where the forward starts");
+  extern __shared__ float2 buf[];
+  __shared__ float red[32];
+  const int batch = blockIdx.y, y0 = blockIdx.x * NB;  // batch = l * C + c
+  const int H = bl.H, W = bl.W, ox = bl.ox;
+  float2* half = V + (size_t)batch * H * N;
+  float2 v[I::GA::MB][I::A];
+  reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
+    const int y = y0 + b;
+    return y < H ? half[((size_t)(a / CB) * H + y) * CB + (a % CB)] : make_float2(0.f, 0.f);
+  });
+  float2 u[I::GC::MB][I::C];
+  I::rest(v, u, buf, tw);
+  const float gscale = 4.0f / ((float)bl.L * (float)bl.C * (float)H * (float)W);
+  const float* tg = target + (size_t)batch * H * W;
+  float acc = 0.f;
+  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+    const int x = a - ox, y = y0 + b;
+    if (x >= 0 && x < W && y < H) {
+      const float I_ = fmaf(val.x, val.x, val.y * val.y);
+      const float d = I_ - __ldg(&tg[(size_t)y * W + x]);
+      acc = fmaf(d, d, acc);
+      val = cscale(val, gscale * d);
+    } else {
+      val = make_float2(0.f, 0.f);
+    }
+  });
+  const float tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  if (!want_grad) return;
+  reg::first_in_regs<N, F::A, NB, T, false>(u);
+  float2 w[F::GC::MB][F::C];
+  F::rest(u, w, buf, tw);
+  reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
+    const int y = y0 + b;
+    if (y < H) half[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
+  });
+}
+
+template <int N, int R0, int R1, int R2, int NB, int T>
+__global__ void __launch_bounds__(T) kr_cols_fwd_planes(const __grid_constant__ BlasmDev bl,
+                                                        const float2* __restrict__ tw,
+                                                        const float2* __restrict__ Y,
+                                                        float2* __restrict__ V) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using F = typename P::F;
+  using I = typename P::I;
+  static_assert(F::C == I::A, "inverse must start where the forward ends");
+  extern __shared__ float2 buf[];
+  const int c = blockIdx.y, kb = blockIdx.x;
+  const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
+  const float2* src = Y + (size_t)c * H * Nx + (size_t)kb * H * NB;
+  float2 v[F::GA::MB][F::A];
+  reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
+    const int y = a - oy;
+    return (y >= 0 && y < H) ? __ldg(&src[(size_t)y * NB + b]) : make_float2(0.f, 0.f);
+  });
+  float2 S[F::GC::MB][F::C];
+  F::rest(v, S, buf, tw);
+  for (int l = 0; l < bl.L; ++l) {
+    const int cl = c * bl.L + l;
+    float2 Z[I::GA::MB][I::A];
+#pragma unroll
+    for (int i = 0; i < I::GA::MB; ++i) {
+      const int q = threadIdx.x + i * T;
+      if (reg::valid<N, I::A, NB, T>(q)) {
+        const int b = q % NB, j = q / NB;
+        const int sx = signed_index(kb * NB + b, Nx);
+#pragma unroll
+        for (int r = 0; r < I::A; ++r) {
+          const int a = j + r * I::GA::M;
+          Z[i][r] = cmul(S[i][r], transfer(bl, cl, sx, signed_index(a, N), bl.inv_ntot));
+        }
+      }
+    }
+    reg::first_in_regs<N, I::A, NB, T, true>(Z);
+    float2 u[I::GC::MB][I::C];
+    I::rest(Z, u, buf, tw);
+    float2* dst = V + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * NB;
+    reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+      const int y = a - oy;
+      if (y >= 0 && y < H) dst[(size_t)y * NB + b] = val;
+    });
+  }
+}
+
+template <int N, int R0, int R1, int R2, int NB, int T>
+__global__ void __launch_bounds__(T) kr_cols_bwd_planes(const __grid_constant__ BlasmDev bl,
+                                                        const float2* __restrict__ tw,
+                                                        const float2* __restrict__ G,
+                                                        float2* __restrict__ D) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using F = typename P::F;
+  using I = typename P::I;
+  static_assert(F::C == I::A, "inverse must start where the forward ends");
+  extern __shared__ float2 buf[];
+  const int c = blockIdx.y, kb = blockIdx.x;
+  const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
+  float2 acc[I::GA::MB][I::A];
+  for (int l = 0; l < bl.L; ++l) {
+    const int cl = c * bl.L + l;
+    const float2* src = G + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * NB;
+    float2 v[F::GA::MB][F::A];
+    reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
+      const int y = a - oy;
+      return (y >= 0 && y < H) ? __ldg(&src[(size_t)y * NB + b]) : make_float2(0.f, 0.f);
+    });
+    float2 S[F::GC::MB][F::C];
+    F::rest(v, S, buf, tw);
+#pragma unroll
+    for (int i = 0; i < F::GC::MB; ++i) {
+      const int q = threadIdx.x + i * T;
+      if (reg::valid<N, F::C, NB, T>(q)) {
+        const int b = q % NB, j = q / NB;
+        const int sx = signed_index(kb * NB + b, Nx);
+#pragma unroll
+        for (int r = 0; r < F::C; ++r) {
+          const int a = j + r * F::GC::M;
+          const float2 t = cmulc(S[i][r], transfer(bl, cl, sx, signed_index(a, N), bl.inv_ntot));
+          acc[i][r] = (l == 0) ? t : cadd(acc[i][r], t);
+        }
+      }
+    }
+  }
+  reg::first_in_regs<N, I::A, NB, T, true>(acc);
+  float2 u[I::GC::MB][I::C];
+  I::rest(acc, u, buf, tw);
+  float2* dst = D + (size_t)c * H * Nx + (size_t)kb * H * NB;
+  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+    const int y = a - oy;
+    if (y >= 0 && y < H) dst[(size_t)y * NB + b] = val;
+  });
+}
+
+// ---------------------------------------------------------------- host launchers
+template <class K>
+inline cudaError_t reg_set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, cudaStream_t s) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  dim3 grid((p->H + NB - 1) / NB, a->batches);
+  const float2* tw = p->fx.tw;
+  cudaError_t e = cudaSuccess;
+  switch (kind) {
+    case SPEC_ROWS_PAD_FWD: {
+      auto k = kr_rows_pad_fwd<N, R0, R1, R2, NB, CB, T>;
+      e = reg_set_smem(k, P::SMEM);
+      if (e != cudaSuccess) return e;
+      prof_begin(KID_ROWS_PAD_FWD, s);
+      k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->in, a->out);
+      prof_end(KID_ROWS_PAD_FWD, s);
+      break;
+    }
+    case SPEC_ROWS_INV_CROP: {
+      auto k = kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T>;
+      e = reg_set_smem(k, P::SMEM);
+      if (e != cudaSuccess) return e;
+      prof_begin(KID_ROWS_INV_CROP, s);
+      k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->in, a->out);
+      prof_end(KID_ROWS_INV_CROP, s);
+      break;
+    }
+    default: {
+      auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
+      e = reg_set_smem(k, P::SMEM);
+      if (e != cudaSuccess) return e;
+      prof_begin(KID_ROWS_LOSS, s);
+      k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad);
+      prof_end(KID_ROWS_LOSS, s);
+      break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+template <int N, int R0, int R1, int R2, int NB, int T>
+cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float2* out,
+                            cudaStream_t s) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  dim3 grid(p->bl.Nx / NB, p->C);
+  const float2* tw = p->fy.tw;
+  cudaError_t e = cudaSuccess;
+  if (kind == SPEC_COLS_FWD_PLANES) {
+    auto k = kr_cols_fwd_planes<N, R0, R1, R2, NB, T>;
+    e = reg_set_smem(k, P::SMEM);
+    if (e != cudaSuccess) return e;
+    prof_begin(KID_COLS_FWD_PLANES, s);
+    k<<<grid, T, P::SMEM, s>>>(p->bl, tw, in, out);
+    prof_end(KID_COLS_FWD_PLANES, s);
+  } else {
+    auto k = kr_cols_bwd_planes<N, R0, R1, R2, NB, T>;
+    e = reg_set_smem(k, P::SMEM);
+    if (e != cudaSuccess) return e;
+    prof_begin(KID_COLS_BWD_PLANES, s);
+    k<<<grid, T, P::SMEM, s>>>(p->bl, tw, in, out);
+    prof_end(KID_COLS_BWD_PLANES, s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace cgh
+
+// One row / column specialisation entry for the spec translation units:
+//   N = R0 * R1 * R2, NB transforms per CTA, CB column-block layout (rows), T threads.
+#define CGH_ROW_SPEC(N, R0, R1, R2, NB, CB, T)                                              \
+  if (N_ == N && RB_ == NB && CB_ == CB) {                                                  \
+    if (!dry) *err = cgh::reg_rows_launch<N, R0, R1, R2, NB, CB, T>(kind, p, a, s);         \
+    return true;                                                                            \
+  }
+#define CGH_COL_SPEC(N, R0, R1, R2, NB, T)                                                  \
+  if (N_ == N && CB_ == NB) {                                                               \
+    if (!dry) *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T>(kind, p, in, out, s);       \
+    return true;                                                                            \
+  }

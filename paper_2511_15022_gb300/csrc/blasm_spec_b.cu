@@ -1,0 +1,15 @@
+// blasm_spec_b.cu -- specialised FFT passes for power-of-two and small padded lengths
+// (the 256x256 hologram pads to 512 x 512).
+#include "blasm_reg.cuh"
+
+bool spec_rows_b(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const SpecRowArgs* a,
+                 cudaStream_t s, cudaError_t* err, bool dry) {
+  CGH_ROW_SPEC(512, 8, 8, 8, 4, 4, 256)
+  return false;
+}
+
+bool spec_cols_b(int kind, int N_, int CB_, const cgh_plan* p, const float2* in, float2* out,
+                 cudaStream_t s, cudaError_t* err, bool dry) {
+  CGH_COL_SPEC(512, 8, 8, 8, 4, 256)
+  return false;
+}

@@ -63,6 +63,7 @@ struct cgh_plan {
   int tiles_x, tiles_y;
   // tuning
   int col_block, row_block, fft_threads, pair_cap_mult;
+  int use_spec;  // 1: use compile-time specialised FFT kernels when one matches
   // FFT descriptors (host copies; tw points into tables_dev)
   FFTDesc fx, fy;
   BlasmDev bl;

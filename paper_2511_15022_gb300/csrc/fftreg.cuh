@@ -1,0 +1,189 @@
+// fftreg.cuh -- compile-time specialised three-pass FFT engine for one CTA (sm_103a).
+//
+// A CTA transforms NB sequences of length N = R0 * R1 * R2 (batch slots b) with T threads.
+// Each pass is a Stockham autosort step (Govindaraju et al., SC'08): butterfly j of radix R
+// with stride Ns reads positions j + r N/R, multiplies by exp(-+2 pi i r (j mod Ns)/(Ns R)),
+// runs an R-point DFT in registers and writes (j - j mod Ns) R + (j mod Ns) + r Ns.  All
+// sizes are template constants, so the index arithmetic folds into shifts and multiplies.
+//
+// Data movement is arranged so that the sequence rarely touches shared memory:
+//   * the first pass reads its inputs through a caller functor (straight from global
+//     memory, skipping known zeros of the padding);
+//   * the last pass leaves its outputs in registers, at natural positions j + r N/R of the
+//     thread that owns butterfly j -- which are exactly the inputs of a following first
+//     pass of the same radix.  So a forward transform can feed a pointwise operation and
+//     an inverse transform without a shared-memory round trip (spectrum x H, loss seed);
+//   * only the two inner exchanges go through shared memory.  The buffer written by a
+//     first pass (stride-R stores) is laid out in rows of R padded to an odd length, which
+//     makes those stores bank-conflict free; the other buffer is dense.  Batch slots are
+//     interleaved innermost ([position][b]).
+// Twiddles: one FP32 table lookup exp(-2 pi i k N/(Ns R) / N) per butterfly (table built in
+// FP64 on the host), higher powers by complex multiplication.
+#pragma once
+
+#include "fft.cuh"
+
+namespace cgh {
+namespace reg {
+
+template <int R>
+struct PadRows {  // odd row length for a buffer written with stride R
+  static constexpr int P = (R % 2) ? R : R + 1;
+};
+
+// Butterfly geometry of one pass.
+template <int N, int R, int NB, int T>
+struct Geo {
+  static constexpr int M = N / R;
+  static constexpr int NBF = M * NB;
+  static constexpr int MB = (NBF + T - 1) / T;
+  static_assert(N % R == 0, "radix must divide N");
+};
+
+// layout of the buffer written by a first pass of radix RW (RW = 0: dense)
+template <int RW, int NB>
+__device__ __forceinline__ int lay(int a, int b) {
+  if constexpr (RW == 0) {
+    return a * NB + b;
+  } else {
+    constexpr int P = PadRows<RW>::P;
+    return ((a / RW) * P + (a % RW)) * NB + b;
+  }
+}
+
+template <int N, int NB, int R0, int R1, int R2>
+struct BufSize {
+  static constexpr int pad(int R) { return (N / R) * ((R % 2) ? R : R + 1); }
+  static constexpr int mx(int a, int b) { return a > b ? a : b; }
+  static constexpr int elems = mx(mx(pad(R0), pad(R2)), N) * NB;
+};
+
+template <int N, int R, int NS, bool INV>
+__device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ tw) {
+  if constexpr (NS > 1) {
+    const int k = j % NS;
+    constexpr int stride = N / (NS * R);
+    float2 w = __ldg(&tw[k * stride]);
+    if (INV) w.y = -w.y;
+    float2 p = w;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      v[r] = cmul(v[r], p);
+      if (r + 1 < R) p = cmul(p, w);
+    }
+  }
+}
+
+template <int N, int R, int NB, int T>
+__device__ __forceinline__ bool valid(int q) {
+  return (Geo<N, R, NB, T>::NBF % T == 0) || q < Geo<N, R, NB, T>::NBF;
+}
+
+// First pass (Ns = 1) with inputs from a functor f(b, a) -> float2.
+template <int N, int R, int NB, int T, bool INV, class F>
+__device__ __forceinline__ void first_from(float2 (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) {
+      const int b = q % NB, j = q / NB;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = f(b, j + r * G::M);
+      DFT<R, INV>::run(v[i]);
+    }
+  }
+}
+
+// First pass (Ns = 1) on values already in registers at positions j + r N/R.
+template <int N, int R, int NB, int T, bool INV>
+__device__ __forceinline__ void first_in_regs(float2 (&v)[Geo<N, R, NB, T>::MB][R]) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) DFT<R, INV>::run(v[i]);
+  }
+}
+
+// Pass with stride NS reading shared memory laid out by RIN (0 = dense).
+template <int N, int R, int NS, int NB, int T, bool INV, int RIN>
+__device__ __forceinline__ void pass_from_smem(float2 (&v)[Geo<N, R, NB, T>::MB][R],
+                                               const float2* buf,
+                                               const float2* __restrict__ tw) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) {
+      const int b = q % NB, j = q / NB;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = buf[lay<RIN, NB>(j + r * G::M, b)];
+      twiddle<N, R, NS, INV>(v[i], j, tw);
+      DFT<R, INV>::run(v[i]);
+    }
+  }
+}
+
+// Store a pass's outputs (stride NS) to shared memory laid out by ROUT (0 = dense).
+template <int N, int R, int NS, int NB, int T, int ROUT>
+__device__ __forceinline__ void pass_to_smem(const float2 (&v)[Geo<N, R, NB, T>::MB][R],
+                                             float2* buf) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) {
+      const int b = q % NB, j = q / NB;
+      const int k = j % NS;
+      const int o = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[lay<ROUT, NB>(o + r * NS, b)] = v[i][r];
+    }
+  }
+}
+
+// Visit the registers of a last pass (natural positions a = j + r N/R): f(b, a, value&).
+template <int N, int R, int NB, int T, class F>
+__device__ __forceinline__ void for_each(float2 (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) {
+      const int b = q % NB, j = q / NB;
+#pragma unroll
+      for (int r = 0; r < R; ++r) f(b, j + r * G::M, v[i][r]);
+    }
+  }
+}
+
+// Three-pass transform helpers.  Forward radix order (R0, R1, R2); inverse (R2, R1, R0).
+// `in` holds the registers of the first pass, already transformed by first_from /
+// first_in_regs; the result is left in `out` (positions j + r N/R_last).  The call starts
+// with a barrier, so buf may still be in use by the previous sequence when it is entered.
+template <int N, int R0, int R1, int R2, int NB, int T, bool INV>
+struct Seq {
+  static constexpr int A = INV ? R2 : R0;  // first radix
+  static constexpr int B = R1;
+  static constexpr int C = INV ? R0 : R2;  // last radix
+  using GA = Geo<N, A, NB, T>;
+  using GB = Geo<N, B, NB, T>;
+  using GC = Geo<N, C, NB, T>;
+
+  __device__ __forceinline__ static void rest(float2 (&in)[GA::MB][A], float2 (&out)[GC::MB][C],
+                                              float2* buf, const float2* __restrict__ tw) {
+    __syncthreads();  // buf may still be read by a previous sequence's last pass
+    pass_to_smem<N, A, 1, NB, T, A>(in, buf);
+    __syncthreads();
+    float2 mid[GB::MB][B];
+    pass_from_smem<N, B, A, NB, T, INV, A>(mid, buf, tw);
+    __syncthreads();
+    pass_to_smem<N, B, A, NB, T, 0>(mid, buf);
+    __syncthreads();
+    pass_from_smem<N, C, A * B, NB, T, INV, 0>(out, buf, tw);
+  }
+};
+
+}  // namespace reg
+}  // namespace cgh

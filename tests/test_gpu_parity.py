@@ -194,11 +194,16 @@ def test_nonfinite_parameters_are_flagged_and_skipped(dev):
     assert rel_l2(U, ref) < FIELD_TOL
 
 
-@pytest.mark.parametrize("tuning", [{"col_block": 1, "row_block": 1},
-                                    {"col_block": 2, "row_block": 3, "fft_threads": 128}])
-def test_tuning_variants_agree(tuning, dev):
+@pytest.mark.parametrize("case,tuning", [
+    ("ragged-100x120-rgb", {"col_block": 1, "row_block": 1}),
+    ("ragged-100x120-rgb", {"col_block": 2, "row_block": 3, "fft_threads": 128}),
+    ("small-256x256", {"fft_kernels": 2}),
+])
+def test_tuning_variants_agree(case, tuning, dev):
+    """Other block shapes, and the generic FFT kernels instead of the specialised ones,
+    give the same step."""
     import torch
-    w = CASES["ragged-100x120-rgb"]
+    w = CASES[case]
     p = inputs.params_for(w)
     T = inputs.blob_targets(w.L, w.C, w.H, w.W)
     pd, Td = to_dev(p, dev), torch.from_numpy(T).to(dev)
