@@ -156,6 +156,13 @@ extern "C" cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L
   bl.oy = (int)((Ny - H) / 2); bl.ox = (int)((Nx - W) / 2);
   bl.inv_ntot = (float)(1.0 / ((double)Ny * (double)Nx));
   bl.aperture2 = (float)(aperture * aperture);
+  bl.series_ok = 1;
+  for (int c = 0; c < C; ++c) {  // largest q = lambda^2 (fx^2 + fy^2) on the padded grid
+    const double fxn = (double)(Nx / 2) / ((double)Nx * pitch_m);
+    const double fyn = (double)(Ny / 2) / ((double)Ny * pitch_m);
+    const double qmax = lambda_m[c] * lambda_m[c] * (fxn * fxn + fyn * fyn);
+    if (!(qmax < 0.04)) bl.series_ok = 0;
+  }
   const double Lx = (double)Nx * pitch_m, Ly = (double)Ny * pitch_m;
   for (int c = 0; c < C; ++c) {
     const double lam = p->lambda[c];

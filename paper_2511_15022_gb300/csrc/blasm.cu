@@ -332,7 +332,8 @@ static bool try_spec_rows(int kind, cgh_plan* p, const SpecRowArgs& a, cudaStrea
 
 static bool try_spec_cols(int kind, cgh_plan* p, const float2* in, float2* out, cudaStream_t s,
                           cudaError_t* err) {
-  if (!p->use_spec) return false;
+  // the specialised column kernels evaluate H with the series form only
+  if (!p->use_spec || !p->bl.series_ok) return false;
   return spec_cols(kind, p->fy.n, p->col_block, p, in, out, s, err, false);
 }
 

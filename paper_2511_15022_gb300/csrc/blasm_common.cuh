@@ -14,6 +14,75 @@ __device__ __forceinline__ int signed_index(int k, int n) { return k < (n + 1) /
 // frac(d / lambda) - (d/lambda) q / (1 + sqrt(1 - q)) with q = lambda^2 (f_x^2 + f_y^2)
 // (the same value as (d / lambda) sqrt(1 - q); the large integer number of turns is removed
 // on the host in FP64).  Evanescent bins inside the band get k_z = 0 (H = 1).
+// Column-invariant part of H_{c,l}: everything that depends on s_x only.
+struct TFCol {
+  float qx2, ax2;  // qx sx^2, ax sx^2
+  float ax_half;   // sx + 1/2 (aperture)
+  bool in_band;    // |s_x| <= kx_max
+};
+
+__device__ __forceinline__ TFCol tf_col(const TFConst& t, int sx) {
+  const float fx2 = (float)(sx * sx);
+  return {t.qx * fx2, t.ax * fx2, (float)sx + 0.5f, abs(sx) <= t.kx_max};
+}
+
+// H_{c,l}(s_x, s_y) * scale from the column part (same formula as transfer() below).
+__device__ __forceinline__ float2 transfer_col(const BlasmDev& bl, const TFConst& t,
+                                               const TFCol& col, int sy, float scale) {
+  if (!col.in_band || abs(sy) > t.ky_max) return make_float2(0.f, 0.f);
+  if (bl.aperture2 > 0.f) {
+    const float ay = (float)sy + 0.5f;
+    if (col.ax_half * col.ax_half + ay * ay >= bl.aperture2) return make_float2(0.f, 0.f);
+  }
+  const float fy2 = (float)(sy * sy);
+  const float q = fmaf(t.qy, fy2, col.qx2);
+  float turns = 0.f;
+  if (q < 1.f) {
+    const float num = fmaf(t.ay, fy2, col.ax2);
+    float g;
+    if (q < 0.05f) {
+      g = fmaf(q, 0.01611328125f, 0.0205078125f);
+      g = fmaf(q, g, 0.02734375f);
+      g = fmaf(q, g, 0.0390625f);
+      g = fmaf(q, g, 0.0625f);
+      g = fmaf(q, g, 0.125f);
+      g = fmaf(q, g, 0.5f);
+    } else {
+      g = 1.f / (1.f + sqrtf(1.f - q));
+    }
+    turns = fmaf(-num, g, t.turns0);
+    turns -= rintf(turns);
+  }
+  float s, c;
+  __sincosf(6.28318530717958647692f * turns, &s, &c);
+  return make_float2(c * scale, s * scale);
+}
+
+// Branch-free H_{c,l} * scale for plans where every bin has q < 0.05 (bl.series_ok, checked
+// on the host): the series for 1 - sqrt(1 - q) applies everywhere, no bin is evanescent,
+// and the band and aperture masks become a select on the scale.
+__device__ __forceinline__ float2 transfer_series(const BlasmDev& bl, const TFConst& t,
+                                                  const TFCol& col, int sy, float scale) {
+  const float fy2 = (float)(sy * sy);
+  const float ay = (float)sy + 0.5f;
+  const bool keep = col.in_band && abs(sy) <= t.ky_max &&
+                    !(bl.aperture2 > 0.f && fmaf(col.ax_half, col.ax_half, ay * ay) >= bl.aperture2);
+  const float q = fmaf(t.qy, fy2, col.qx2);
+  const float num = fmaf(t.ay, fy2, col.ax2);
+  float g = fmaf(q, 0.01611328125f, 0.0205078125f);
+  g = fmaf(q, g, 0.02734375f);
+  g = fmaf(q, g, 0.0390625f);
+  g = fmaf(q, g, 0.0625f);
+  g = fmaf(q, g, 0.125f);
+  g = fmaf(q, g, 0.5f);
+  float turns = fmaf(-num, g, t.turns0);
+  turns -= rintf(turns);
+  float s, c;
+  __sincosf(6.28318530717958647692f * turns, &s, &c);
+  const float sc = keep ? scale : 0.f;
+  return make_float2(c * sc, s * sc);
+}
+
 __device__ __forceinline__ float2 transfer(const BlasmDev& bl, int cl, int sx, int sy,
                                            float scale) {
   const TFConst& t = bl.tf[cl];
@@ -26,9 +95,22 @@ __device__ __forceinline__ float2 transfer(const BlasmDev& bl, int cl, int sx, i
   const float q = fmaf(t.qx, fx2, t.qy * fy2);
   float turns = 0.f;
   if (q < 1.f) {
-    const float den = 1.f + sqrtf(1.f - q);
+    // (d/lambda) (1 - sqrt(1 - q)) = num * g(q), num = (d/lambda) q.  For q < 0.05 g is the
+    // binomial series of (1 - sqrt(1 - q)) / q, truncated after q^6 (remainder < 3e-10
+    // relative); otherwise the closed form 1 / (1 + sqrt(1 - q)).
     const float num = fmaf(t.ax, fx2, t.ay * fy2);
-    turns = t.turns0 - num / den;
+    float g;
+    if (q < 0.05f) {
+      g = fmaf(q, 0.01611328125f, 0.0205078125f);  // 33/2048, 21/1024
+      g = fmaf(q, g, 0.02734375f);                  // 7/256
+      g = fmaf(q, g, 0.0390625f);                   // 5/128
+      g = fmaf(q, g, 0.0625f);                      // 1/16
+      g = fmaf(q, g, 0.125f);                       // 1/8
+      g = fmaf(q, g, 0.5f);                         // 1/2
+    } else {
+      g = 1.f / (1.f + sqrtf(1.f - q));
+    }
+    turns = fmaf(-num, g, t.turns0);
     turns -= rintf(turns);
   }
   // |turns| <= 1/2 after the exact reduction above: the hardware sine/cosine on

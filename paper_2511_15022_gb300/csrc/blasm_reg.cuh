@@ -16,18 +16,26 @@
 #include "blasm_spec.h"
 #include "fftreg.cuh"
 
+// resident CTAs per SM the register allocation is sized for
+#ifndef CGH_REG_MINB
+#define CGH_REG_MINB(T) ((T) <= 256 ? 3 : 2)
+#endif
+
 namespace cgh {
 
-template <int N, int R0, int R1, int R2, int NB, int T>
+template <int N, int R0, int R1, int R2, int NB, int T, class E = float2>
 struct RegPlan {
-  using F = reg::Seq<N, R0, R1, R2, NB, T, false>;
-  using I = reg::Seq<N, R0, R1, R2, NB, T, true>;
+  using F = reg::Seq<N, R0, R1, R2, NB, T, false, E>;
+  using I = reg::Seq<N, R0, R1, R2, NB, T, true, E>;
   static constexpr int BUF = reg::BufSize<N, NB, R0, R1, R2>::elems;
-  static constexpr size_t SMEM = sizeof(float2) * (size_t)BUF;
+  static constexpr size_t SMEM = sizeof(E) * (size_t)BUF;
+  // exchange buffer + one thread-private slot per register of a last pass (column kernels)
+  static constexpr size_t SMEM_SLOTS =
+      SMEM + sizeof(E) * (size_t)F::GC::MB * F::C * T;
 };
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
-__global__ void __launch_bounds__(T) kr_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
+__global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
                                                      const float2* __restrict__ tw,
                                                      const float2* __restrict__ in,
                                                      float2* __restrict__ half) {
@@ -52,7 +60,7 @@ __global__ void __launch_bounds__(T) kr_rows_pad_fwd(const __grid_constant__ Bla
 }
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
-__global__ void __launch_bounds__(T) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
+__global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
                                                       const float2* __restrict__ tw,
                                                       const float2* __restrict__ half,
                                                       float2* __restrict__ out) {
@@ -77,7 +85,7 @@ __global__ void __launch_bounds__(T) kr_rows_inv_crop(const __grid_constant__ Bl
 }
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
-__global__ void __launch_bounds__(T) kr_rows_loss(const __grid_constant__ BlasmDev bl,
+__global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_constant__ BlasmDev bl,
                                                   const float2* __restrict__ tw,
                                                   float2* __restrict__ V,
                                                   const float* __restrict__ target,
@@ -124,105 +132,139 @@ __global__ void __launch_bounds__(T) kr_rows_loss(const __grid_constant__ BlasmD
   });
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T>
-__global__ void __launch_bounds__(T) kr_cols_fwd_planes(const __grid_constant__ BlasmDev bl,
+// Column kernels work on float4 elements: columns 2 s and 2 s + 1 of the CTA's column block
+// transformed in lockstep (NB float4 slots, CB = 2 NB columns per CTA).
+__device__ __forceinline__ float4 transfer_pair(const BlasmDev& bl, const TFConst& t,
+                                                const TFCol& c0, const TFCol& c1, int sy,
+                                                float4 v, bool conj_h) {
+  const float2 h0 = transfer_series(bl, t, c0, sy, bl.inv_ntot);
+  const float2 h1 = transfer_series(bl, t, c1, sy, bl.inv_ntot);
+  return conj_h ? pack(cmulc(lo(v), h0), cmulc(hi(v), h1)) : pack(cmul(lo(v), h0), cmul(hi(v), h1));
+}
+
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_constant__ BlasmDev bl,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ Y,
                                                         float2* __restrict__ V) {
-  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
   using F = typename P::F;
   using I = typename P::I;
   static_assert(F::C == I::A, "inverse must start where the forward ends");
-  extern __shared__ float2 buf[];
+  constexpr int CB = 2 * NB;
+  extern __shared__ float4 buf4[];
   const int c = blockIdx.y, kb = blockIdx.x;
   const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
-  const float2* src = Y + (size_t)c * H * Nx + (size_t)kb * H * NB;
-  float2 v[F::GA::MB][F::A];
+  const float4* src = reinterpret_cast<const float4*>(Y + (size_t)c * H * Nx + (size_t)kb * H * CB);
+  float4 v[F::GA::MB][F::A];
   reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
     const int y = a - oy;
-    return (y >= 0 && y < H) ? __ldg(&src[(size_t)y * NB + b]) : make_float2(0.f, 0.f);
+    return (y >= 0 && y < H) ? __ldg(&src[y * NB + b]) : make_float4(0.f, 0.f, 0.f, 0.f);
   });
-  float2 S[F::GC::MB][F::C];
-  F::rest(v, S, buf, tw);
+  // the spectrum is parked in thread-private shared-memory slots (one 16-byte load per
+  // element per plane) so that the inverse passes get the registers
+  float4* spec = buf4 + P::BUF;
+  {
+    float4 S[F::GC::MB][F::C];
+    F::rest(v, S, buf4, tw);
+#pragma unroll
+    for (int i = 0; i < F::GC::MB; ++i)
+#pragma unroll
+      for (int r = 0; r < F::C; ++r) spec[(i * F::C + r) * T + threadIdx.x] = S[i][r];
+  }
   for (int l = 0; l < bl.L; ++l) {
-    const int cl = c * bl.L + l;
-    float2 Z[I::GA::MB][I::A];
+    const TFConst& tc = bl.tf[c * bl.L + l];
+    float4 Z[I::GA::MB][I::A];
 #pragma unroll
     for (int i = 0; i < I::GA::MB; ++i) {
       const int q = threadIdx.x + i * T;
       if (reg::valid<N, I::A, NB, T>(q)) {
         const int b = q % NB, j = q / NB;
-        const int sx = signed_index(kb * NB + b, Nx);
+        const TFCol c0 = tf_col(tc, signed_index(kb * CB + 2 * b, Nx));
+        const TFCol c1 = tf_col(tc, signed_index(kb * CB + 2 * b + 1, Nx));
 #pragma unroll
-        for (int r = 0; r < I::A; ++r) {
-          const int a = j + r * I::GA::M;
-          Z[i][r] = cmul(S[i][r], transfer(bl, cl, sx, signed_index(a, N), bl.inv_ntot));
-        }
+        for (int r = 0; r < I::A; ++r)
+          Z[i][r] = transfer_pair(bl, tc, c0, c1, signed_index(j + r * I::GA::M, N),
+                                  spec[(i * I::A + r) * T + threadIdx.x], false);
       }
     }
     reg::first_in_regs<N, I::A, NB, T, true>(Z);
-    float2 u[I::GC::MB][I::C];
-    I::rest(Z, u, buf, tw);
-    float2* dst = V + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * NB;
-    reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+    float4 u[I::GC::MB][I::C];
+    I::rest(Z, u, buf4, tw);
+    float4* dst = reinterpret_cast<float4*>(V + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB);
+    reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float4& val) {
       const int y = a - oy;
-      if (y >= 0 && y < H) dst[(size_t)y * NB + b] = val;
+      if (y >= 0 && y < H) dst[y * NB + b] = val;
     });
   }
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T>
-__global__ void __launch_bounds__(T) kr_cols_bwd_planes(const __grid_constant__ BlasmDev bl,
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
+__global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_constant__ BlasmDev bl,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ G,
                                                         float2* __restrict__ D) {
-  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
   using F = typename P::F;
   using I = typename P::I;
   static_assert(F::C == I::A, "inverse must start where the forward ends");
-  extern __shared__ float2 buf[];
+  constexpr int CB = 2 * NB;
+  extern __shared__ float4 buf4[];
   const int c = blockIdx.y, kb = blockIdx.x;
   const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
-  float2 acc[I::GA::MB][I::A];
+  // the running sum over planes lives in thread-private shared-memory slots
+  float4* accs = buf4 + P::BUF;
   for (int l = 0; l < bl.L; ++l) {
-    const int cl = c * bl.L + l;
-    const float2* src = G + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * NB;
-    float2 v[F::GA::MB][F::A];
+    const TFConst& tc = bl.tf[c * bl.L + l];
+    const float4* src =
+        reinterpret_cast<const float4*>(G + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB);
+    float4 v[F::GA::MB][F::A];
     reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
       const int y = a - oy;
-      return (y >= 0 && y < H) ? __ldg(&src[(size_t)y * NB + b]) : make_float2(0.f, 0.f);
+      return (y >= 0 && y < H) ? __ldg(&src[y * NB + b]) : make_float4(0.f, 0.f, 0.f, 0.f);
     });
-    float2 S[F::GC::MB][F::C];
-    F::rest(v, S, buf, tw);
+    float4 S[F::GC::MB][F::C];
+    F::rest(v, S, buf4, tw);
 #pragma unroll
     for (int i = 0; i < F::GC::MB; ++i) {
       const int q = threadIdx.x + i * T;
       if (reg::valid<N, F::C, NB, T>(q)) {
         const int b = q % NB, j = q / NB;
-        const int sx = signed_index(kb * NB + b, Nx);
+        const TFCol c0 = tf_col(tc, signed_index(kb * CB + 2 * b, Nx));
+        const TFCol c1 = tf_col(tc, signed_index(kb * CB + 2 * b + 1, Nx));
 #pragma unroll
         for (int r = 0; r < F::C; ++r) {
-          const int a = j + r * F::GC::M;
-          const float2 t = cmulc(S[i][r], transfer(bl, cl, sx, signed_index(a, N), bl.inv_ntot));
-          acc[i][r] = (l == 0) ? t : cadd(acc[i][r], t);
+          const float4 t = transfer_pair(bl, tc, c0, c1, signed_index(j + r * F::GC::M, N), S[i][r], true);
+          float4& a = accs[(i * F::C + r) * T + threadIdx.x];
+          a = (l == 0) ? t : cadd(a, t);
         }
       }
     }
   }
+  float4 acc[I::GA::MB][I::A];
+#pragma unroll
+  for (int i = 0; i < I::GA::MB; ++i)
+#pragma unroll
+    for (int r = 0; r < I::A; ++r) acc[i][r] = accs[(i * I::A + r) * T + threadIdx.x];
   reg::first_in_regs<N, I::A, NB, T, true>(acc);
-  float2 u[I::GC::MB][I::C];
-  I::rest(acc, u, buf, tw);
-  float2* dst = D + (size_t)c * H * Nx + (size_t)kb * H * NB;
-  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+  float4 u[I::GC::MB][I::C];
+  I::rest(acc, u, buf4, tw);
+  float4* dst = reinterpret_cast<float4*>(D + (size_t)c * H * Nx + (size_t)kb * H * CB);
+  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float4& val) {
     const int y = a - oy;
-    if (y >= 0 && y < H) dst[(size_t)y * NB + b] = val;
+    if (y >= 0 && y < H) dst[y * NB + b] = val;
   });
 }
 
 // ---------------------------------------------------------------- host launchers
 template <class K>
 inline cudaError_t reg_set_smem(K kernel, size_t bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  // the L1 / shared split is otherwise chosen per launch and can cap residency at one CTA
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
@@ -263,26 +305,27 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
   return cudaGetLastError();
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T>
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
 cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float2* out,
                             cudaStream_t s) {
-  using P = RegPlan<N, R0, R1, R2, NB, T>;
-  dim3 grid(p->bl.Nx / NB, p->C);
+  using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
+  static_assert(P::F::C == P::I::A, "slot layout shared by the forward end and inverse start");
+  dim3 grid(p->bl.Nx / (2 * NB), p->C);
   const float2* tw = p->fy.tw;
   cudaError_t e = cudaSuccess;
   if (kind == SPEC_COLS_FWD_PLANES) {
-    auto k = kr_cols_fwd_planes<N, R0, R1, R2, NB, T>;
-    e = reg_set_smem(k, P::SMEM);
+    auto k = kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB>;
+    e = reg_set_smem(k, P::SMEM_SLOTS);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
-    k<<<grid, T, P::SMEM, s>>>(p->bl, tw, in, out);
+    k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
-    auto k = kr_cols_bwd_planes<N, R0, R1, R2, NB, T>;
-    e = reg_set_smem(k, P::SMEM);
+    auto k = kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB>;
+    e = reg_set_smem(k, P::SMEM_SLOTS);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
-    k<<<grid, T, P::SMEM, s>>>(p->bl, tw, in, out);
+    k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);
     prof_end(KID_COLS_BWD_PLANES, s);
   }
   return cudaGetLastError();
@@ -297,8 +340,10 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
     if (!dry) *err = cgh::reg_rows_launch<N, R0, R1, R2, NB, CB, T>(kind, p, a, s);         \
     return true;                                                                            \
   }
-#define CGH_COL_SPEC(N, R0, R1, R2, NB, T)                                                  \
-  if (N_ == N && CB_ == NB) {                                                               \
-    if (!dry) *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T>(kind, p, in, out, s);       \
+//   column entries: NB float4 slots per CTA, i.e. CB = 2 NB columns; MINB resident CTAs per
+//   SM the registers are sized for.
+#define CGH_COL_SPEC(N, R0, R1, R2, NB, T, MINB)                                            \
+  if (N_ == N && CB_ == 2 * (NB)) {                                                         \
+    if (!dry) *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T, MINB>(kind, p, in, out, s); \
     return true;                                                                            \
   }

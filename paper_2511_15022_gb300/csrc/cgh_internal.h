@@ -49,6 +49,7 @@ struct BlasmDev {
   int oy, ox;      // offset of the image window inside the padded grid
   float inv_ntot;  // 1 / (Ny * Nx)
   float aperture2; // aperture radius^2 in index units (0 = off)
+  int series_ok;   // every bin has q = lambda^2 (fx^2 + fy^2) < 0.05 (see transfer_series)
   TFConst tf[CGH_MAX_C * CGH_MAX_L];  // index c * L + l
 };
 

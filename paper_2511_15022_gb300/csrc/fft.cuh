@@ -87,6 +87,10 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// y + s x
+__device__ __forceinline__ float2 caxpy(float s, float2 x, float2 y) {
+  return make_float2(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y));
+}
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 z) {
@@ -116,19 +120,42 @@ __device__ __forceinline__ float2 twmul(float2 x) {
   }
 }
 
+// float4 = two complex numbers (x, y) and (z, w) transformed in lockstep (two columns that
+// share one butterfly's index arithmetic and twiddles).
+__device__ __forceinline__ float2 lo(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float4 pack(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) { return pack(cadd(lo(a), lo(b)), cadd(hi(a), hi(b))); }
+__device__ __forceinline__ float4 csub(float4 a, float4 b) { return pack(csub(lo(a), lo(b)), csub(hi(a), hi(b))); }
+__device__ __forceinline__ float4 cmul(float4 a, float2 b) { return pack(cmul(lo(a), b), cmul(hi(a), b)); }
+__device__ __forceinline__ float4 cscale(float4 a, float s) { return pack(cscale(lo(a), s), cscale(hi(a), s)); }
+__device__ __forceinline__ float4 caxpy(float s, float4 x, float4 y) {
+  return pack(caxpy(s, lo(x), lo(y)), caxpy(s, hi(x), hi(y)));
+}
+template <bool INV>
+__device__ __forceinline__ float4 mul_mi(float4 z) { return pack(mul_mi<INV>(lo(z)), mul_mi<INV>(hi(z))); }
+template <int K, int N, bool INV>
+__device__ __forceinline__ float4 twmul(float4 x) {
+  return pack(twmul<K, N, INV>(lo(x)), twmul<K, N, INV>(hi(x)));
+}
+
 // ---------------------------------------------------------------- R-point DFT codelets
+// DFT<R, INV>::run(v) transforms R elements in place; E is float2 (one complex number) or
+// float4 (two in lockstep).
 template <int R, bool INV>
 struct DFT;
 
 template <bool INV>
 struct DFT<1, INV> {
-  __device__ __forceinline__ static void run(float2 (&)[1]) {}
+  template <class E>
+  __device__ __forceinline__ static void run(E (&)[1]) {}
 };
 
 template <bool INV>
 struct DFT<2, INV> {
-  __device__ __forceinline__ static void run(float2 (&v)[2]) {
-    float2 a = v[0], b = v[1];
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[2]) {
+    const E a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
   }
@@ -136,11 +163,12 @@ struct DFT<2, INV> {
 
 template <bool INV>
 struct DFT<3, INV> {
-  __device__ __forceinline__ static void run(float2 (&v)[3]) {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[3]) {
     constexpr float h = 0.86602540378443864676f;  // sin(2 pi / 3)
-    float2 t1 = cadd(v[1], v[2]);
-    float2 t2 = mul_mi<INV>(cscale(csub(v[1], v[2]), h));
-    float2 m = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+    const E t1 = cadd(v[1], v[2]);
+    const E t2 = mul_mi<INV>(cscale(csub(v[1], v[2]), h));
+    const E m = caxpy(-0.5f, t1, v[0]);
     v[0] = cadd(v[0], t1);
     v[1] = cadd(m, t2);
     v[2] = csub(m, t2);
@@ -149,9 +177,10 @@ struct DFT<3, INV> {
 
 template <bool INV>
 struct DFT<4, INV> {
-  __device__ __forceinline__ static void run(float2 (&v)[4]) {
-    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    float2 t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[4]) {
+    const E t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    const E t2 = cadd(v[1], v[3]), t3 = mul_mi<INV>(csub(v[1], v[3]));
     v[0] = cadd(t0, t2);
     v[2] = csub(t0, t2);
     v[1] = cadd(t1, t3);
@@ -161,19 +190,20 @@ struct DFT<4, INV> {
 
 template <bool INV>
 struct DFT<5, INV> {
-  __device__ __forceinline__ static void run(float2 (&v)[5]) {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[5]) {
     constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
     constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
     constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
     constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
-    float2 a = cadd(v[1], v[4]), b = csub(v[1], v[4]);
-    float2 c = cadd(v[2], v[3]), d = csub(v[2], v[3]);
-    float2 x0 = v[0];
-    float2 r1 = make_float2(x0.x + c1 * a.x + c2 * c.x, x0.y + c1 * a.y + c2 * c.y);
-    float2 r2 = make_float2(x0.x + c2 * a.x + c1 * c.x, x0.y + c2 * a.y + c1 * c.y);
-    float2 i1 = mul_mi<INV>(make_float2(s1 * b.x + s2 * d.x, s1 * b.y + s2 * d.y));
-    float2 i2 = mul_mi<INV>(make_float2(s2 * b.x - s1 * d.x, s2 * b.y - s1 * d.y));
-    v[0] = make_float2(x0.x + a.x + c.x, x0.y + a.y + c.y);
+    const E a = cadd(v[1], v[4]), b = csub(v[1], v[4]);
+    const E c = cadd(v[2], v[3]), d = csub(v[2], v[3]);
+    const E x0 = v[0];
+    const E r1 = caxpy(c2, c, caxpy(c1, a, x0));
+    const E r2 = caxpy(c1, c, caxpy(c2, a, x0));
+    const E i1 = mul_mi<INV>(caxpy(s2, d, cscale(b, s1)));
+    const E i2 = mul_mi<INV>(caxpy(-s1, d, cscale(b, s2)));
+    v[0] = cadd(x0, cadd(a, c));
     v[1] = cadd(r1, i1);
     v[4] = csub(r1, i1);
     v[2] = cadd(r2, i2);
@@ -191,12 +221,13 @@ struct SplitOf {
 template <int R, bool INV>
 struct DFT {
   static_assert(R % SplitOf<R>::A == 0, "unsupported radix");
-  __device__ __forceinline__ static void run(float2 (&v)[R]) {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[R]) {
     constexpr int A = SplitOf<R>::A, B = SplitOf<R>::B;
-    float2 u[B][A];
+    E u[B][A];
     sfor<0, B>([&](auto N2) {
       constexpr int n2 = decltype(N2)::value;
-      float2 t[A];
+      E t[A];
       sfor<0, A>([&](auto N1) { t[decltype(N1)::value] = v[B * decltype(N1)::value + n2]; });
       DFT<A, INV>::run(t);
       sfor<0, A>([&](auto K1) {
@@ -206,7 +237,7 @@ struct DFT {
     });
     sfor<0, A>([&](auto K1) {
       constexpr int k1 = decltype(K1)::value;
-      float2 t[B];
+      E t[B];
       sfor<0, B>([&](auto N2) { t[decltype(N2)::value] = u[decltype(N2)::value][k1]; });
       DFT<B, INV>::run(t);
       sfor<0, B>([&](auto K2) { v[k1 + A * decltype(K2)::value] = t[decltype(K2)::value]; });

@@ -1,6 +1,8 @@
 // fftreg.cuh -- compile-time specialised three-pass FFT engine for one CTA (sm_103a).
 //
 // A CTA transforms NB sequences of length N = R0 * R1 * R2 (batch slots b) with T threads.
+// Elements are float2 (one complex number) or float4 (two sequences in lockstep, sharing
+// every index computation and twiddle).
 // Each pass is a Stockham autosort step (Govindaraju et al., SC'08): butterfly j of radix R
 // with stride Ns reads positions j + r N/R, multiplies by exp(-+2 pi i r (j mod Ns)/(Ns R)),
 // runs an R-point DFT in registers and writes (j - j mod Ns) R + (j mod Ns) + r Ns.  All
@@ -17,8 +19,9 @@
 //     first pass (stride-R stores) is laid out in rows of R padded to an odd length, which
 //     makes those stores bank-conflict free; the other buffer is dense.  Batch slots are
 //     interleaved innermost ([position][b]).
-// Twiddles: one FP32 table lookup exp(-2 pi i k N/(Ns R) / N) per butterfly (table built in
-// FP64 on the host), higher powers by complex multiplication.
+// Twiddles: one FP32 table lookup exp(-2 pi i k / (Ns R)) per butterfly (table built in FP64
+// on the host), higher powers by complex multiplication; shared-memory addresses of every
+// pass are base + r * stride.
 #pragma once
 
 #include "fft.cuh"
@@ -58,12 +61,14 @@ struct BufSize {
   static constexpr int elems = mx(mx(pad(R0), pad(R2)), N) * NB;
 };
 
-template <int N, int R, int NS, bool INV>
-__device__ __forceinline__ void twiddle(float2 (&v)[R], int j, const float2* __restrict__ tw) {
+template <int N, int R, int NS, bool INV, class E>
+__device__ __forceinline__ void twiddle(E (&v)[R], int j, const float2* __restrict__ tw) {
   if constexpr (NS > 1) {
+    // one lookup of exp(-2 pi i k / (NS R)); its powers by complex multiplication (a
+    // lookup per power was slower: load latency at this occupancy outweighs 4 FMAs)
     const int k = j % NS;
     constexpr int stride = N / (NS * R);
-    float2 w = __ldg(&tw[k * stride]);
+    float2 w = __ldg(tw + k * stride);
     if (INV) w.y = -w.y;
     float2 p = w;
 #pragma unroll
@@ -80,8 +85,8 @@ __device__ __forceinline__ bool valid(int q) {
 }
 
 // First pass (Ns = 1) with inputs from a functor f(b, a) -> float2.
-template <int N, int R, int NB, int T, bool INV, class F>
-__device__ __forceinline__ void first_from(float2 (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
+template <int N, int R, int NB, int T, bool INV, class E, class F>
+__device__ __forceinline__ void first_from(E (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
   for (int i = 0; i < G::MB; ++i) {
@@ -96,8 +101,8 @@ __device__ __forceinline__ void first_from(float2 (&v)[Geo<N, R, NB, T>::MB][R],
 }
 
 // First pass (Ns = 1) on values already in registers at positions j + r N/R.
-template <int N, int R, int NB, int T, bool INV>
-__device__ __forceinline__ void first_in_regs(float2 (&v)[Geo<N, R, NB, T>::MB][R]) {
+template <int N, int R, int NB, int T, bool INV, class E>
+__device__ __forceinline__ void first_in_regs(E (&v)[Geo<N, R, NB, T>::MB][R]) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
   for (int i = 0; i < G::MB; ++i) {
@@ -107,9 +112,9 @@ __device__ __forceinline__ void first_in_regs(float2 (&v)[Geo<N, R, NB, T>::MB][
 }
 
 // Pass with stride NS reading shared memory laid out by RIN (0 = dense).
-template <int N, int R, int NS, int NB, int T, bool INV, int RIN>
-__device__ __forceinline__ void pass_from_smem(float2 (&v)[Geo<N, R, NB, T>::MB][R],
-                                               const float2* buf,
+template <int N, int R, int NS, int NB, int T, bool INV, int RIN, class E>
+__device__ __forceinline__ void pass_from_smem(E (&v)[Geo<N, R, NB, T>::MB][R],
+                                               const E* buf,
                                                const float2* __restrict__ tw) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
@@ -117,35 +122,54 @@ __device__ __forceinline__ void pass_from_smem(float2 (&v)[Geo<N, R, NB, T>::MB]
     const int q = threadIdx.x + i * T;
     if (valid<N, R, NB, T>(q)) {
       const int b = q % NB, j = q / NB;
+      // positions j + r M are linear in r in both layouts (M is a multiple of RIN)
+      int base, stride;
+      if constexpr (RIN == 0) {
+        base = j * NB + b;
+        stride = G::M * NB;
+      } else {
+        static_assert(G::M % RIN == 0, "padded rows must tile the read stride");
+        constexpr int P = PadRows<RIN>::P;
+        base = ((j / RIN) * P + (j % RIN)) * NB + b;
+        stride = (G::M / RIN) * P * NB;
+      }
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = buf[lay<RIN, NB>(j + r * G::M, b)];
-      twiddle<N, R, NS, INV>(v[i], j, tw);
+      for (int r = 0; r < R; ++r) v[i][r] = buf[base + r * stride];
+      twiddle<N, R, NS, INV, E>(v[i], j, tw);
       DFT<R, INV>::run(v[i]);
     }
   }
 }
 
 // Store a pass's outputs (stride NS) to shared memory laid out by ROUT (0 = dense).
-template <int N, int R, int NS, int NB, int T, int ROUT>
-__device__ __forceinline__ void pass_to_smem(const float2 (&v)[Geo<N, R, NB, T>::MB][R],
-                                             float2* buf) {
+template <int N, int R, int NS, int NB, int T, int ROUT, class E>
+__device__ __forceinline__ void pass_to_smem(const E (&v)[Geo<N, R, NB, T>::MB][R], E* buf) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
   for (int i = 0; i < G::MB; ++i) {
     const int q = threadIdx.x + i * T;
     if (valid<N, R, NB, T>(q)) {
       const int b = q % NB, j = q / NB;
-      const int k = j % NS;
-      const int o = (j - k) * R + k;
+      int base, stride;
+      if constexpr (ROUT == 0) {
+        const int k = j % NS;
+        base = ((j - k) * R + k) * NB + b;
+        stride = NS * NB;
+      } else {
+        // first pass (NS = 1) into rows of R padded to P: position j R + r -> row j, col r
+        static_assert(ROUT == R && NS == 1, "padded layout is written by a first pass");
+        base = j * PadRows<R>::P * NB + b;
+        stride = NB;
+      }
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[lay<ROUT, NB>(o + r * NS, b)] = v[i][r];
+      for (int r = 0; r < R; ++r) buf[base + r * stride] = v[i][r];
     }
   }
 }
 
 // Visit the registers of a last pass (natural positions a = j + r N/R): f(b, a, value&).
-template <int N, int R, int NB, int T, class F>
-__device__ __forceinline__ void for_each(float2 (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
+template <int N, int R, int NB, int T, class E, class F>
+__device__ __forceinline__ void for_each(E (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
   for (int i = 0; i < G::MB; ++i) {
@@ -162,7 +186,7 @@ __device__ __forceinline__ void for_each(float2 (&v)[Geo<N, R, NB, T>::MB][R], F
 // `in` holds the registers of the first pass, already transformed by first_from /
 // first_in_regs; the result is left in `out` (positions j + r N/R_last).  The call starts
 // with a barrier, so buf may still be in use by the previous sequence when it is entered.
-template <int N, int R0, int R1, int R2, int NB, int T, bool INV>
+template <int N, int R0, int R1, int R2, int NB, int T, bool INV, class E = float2>
 struct Seq {
   static constexpr int A = INV ? R2 : R0;  // first radix
   static constexpr int B = R1;
@@ -171,17 +195,17 @@ struct Seq {
   using GB = Geo<N, B, NB, T>;
   using GC = Geo<N, C, NB, T>;
 
-  __device__ __forceinline__ static void rest(float2 (&in)[GA::MB][A], float2 (&out)[GC::MB][C],
-                                              float2* buf, const float2* __restrict__ tw) {
+  __device__ __forceinline__ static void rest(E (&in)[GA::MB][A], E (&out)[GC::MB][C], E* buf,
+                                              const float2* __restrict__ tw) {
     __syncthreads();  // buf may still be read by a previous sequence's last pass
-    pass_to_smem<N, A, 1, NB, T, A>(in, buf);
+    pass_to_smem<N, A, 1, NB, T, A, E>(in, buf);
     __syncthreads();
-    float2 mid[GB::MB][B];
-    pass_from_smem<N, B, A, NB, T, INV, A>(mid, buf, tw);
+    E mid[GB::MB][B];
+    pass_from_smem<N, B, A, NB, T, INV, A, E>(mid, buf, tw);
     __syncthreads();
-    pass_to_smem<N, B, A, NB, T, 0>(mid, buf);
+    pass_to_smem<N, B, A, NB, T, 0, E>(mid, buf);
     __syncthreads();
-    pass_from_smem<N, C, A * B, NB, T, INV, 0>(out, buf, tw);
+    pass_from_smem<N, C, A * B, NB, T, INV, 0, E>(out, buf, tw);
   }
 };
 

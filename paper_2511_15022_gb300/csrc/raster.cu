@@ -265,6 +265,34 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float
   }
 }
 
+// Warp reduce-scatter of COUNT values per lane (COUNT a power of two <= 32): at each step
+// lanes exchange half of their values with the partner OFF lanes away and keep the sum of
+// the other half, so COUNT values cost COUNT - 1 + log2(32 / COUNT) shuffles instead of
+// 5 * COUNT.  Afterwards every lane holds the warp total of value `base`; lanes that differ
+// only in the bits below log2(32 / COUNT) hold the same value.
+template <int COUNT, int OFF>
+struct ReduceScatter {
+  __device__ __forceinline__ static void run(float* cur, int lane, int& base) {
+    constexpr int HALF = COUNT / 2;
+    const bool hi = (lane & OFF) != 0;
+#pragma unroll
+    for (int i = 0; i < HALF; ++i) {
+      const float send = hi ? cur[i] : cur[i + HALF];
+      const float keep = hi ? cur[i + HALF] : cur[i];
+      cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, OFF);
+    }
+    if (hi) base += HALF;
+    ReduceScatter<HALF, OFF / 2>::run(cur, lane, base);
+  }
+};
+template <int OFF>
+struct ReduceScatter<1, OFF> {
+  __device__ __forceinline__ static void run(float* cur, int, int&) {
+#pragma unroll
+    for (int o = OFF; o >= 1; o >>= 1) cur[0] += __shfl_xor_sync(0xffffffffu, cur[0], o);
+  }
+};
+
 // Raw accumulated moments per Gaussian (NV = 2C + 6 values):
 //   [0, C)      P_c = sum a dL/dRe_c          [C, 2C)  Q_c = sum a dL/dIm_c
 //   2C          SG  = sum G S (unclamped pairs), S = sum_c (A_c dRe_c + B_c dIm_c)
@@ -277,6 +305,7 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
                                                     const float2* __restrict__ dU,
                                                     float* __restrict__ raw) {
   constexpr int NV = 2 * C + 6;
+  constexpr int NVP = NV <= 8 ? 8 : 16;  // padded to a power of two for the reduce-scatter
   __shared__ float4 srec[256 * CGH_REC_F4];
   __shared__ float sacc[256 * NV];
   __shared__ int sgid[256];
@@ -317,9 +346,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
       const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
       const bool pass = inside && p2 >= r1.y;
       if (!__any_sync(0xffffffffu, pass)) continue;
-      float val[NV];
+      float val[NVP];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) val[v] = 0.f;
+      for (int v = 0; v < NVP; ++v) val[v] = 0.f;
       if (pass) {
         const float4 r3 = srec[j * CGH_REC_F4 + 3];
         const float4 r4 = srec[j * CGH_REC_F4 + 4];
@@ -348,15 +377,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
           }
         }
       }
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) val[v] += __shfl_xor_sync(0xffffffffu, val[v], o);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) atomicAdd(&sacc[j * NV + v], val[v]);
-      }
+      int vidx = 0;
+      ReduceScatter<NVP, 16>::run(val, lane, vidx);
+      if ((lane & (32 / NVP - 1)) == 0 && vidx < NV) atomicAdd(&sacc[j * NV + vidx], val[0]);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nb * NV; t += 256) {
