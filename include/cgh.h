@@ -141,6 +141,23 @@ cgh_status cgh_plan_status(cgh_plan* plan, int64_t* pairs_needed, int32_t* overf
 cgh_status cgh_raster_fwd(cgh_plan* plan, const cgh_params* params, void* U_out,
                           void* stream);
 
+/* Forward rasterisation that allocates nothing and needs no plan.  The paper has no
+ * counterpart: this exists for callers that may not allocate device memory -- e.g. an
+ * application that reserves all device memory at start-up, or a latency-critical loop where
+ * cudaMalloc's implicit device-wide synchronisation is not acceptable.  It computes the same
+ * field as cgh_raster_fwd (H x W pixels, C channels 1..4, skip threshold `cutoff`; U_out
+ * [C][H][W] complex, caller-allocated), keeping its binning scratch in one fixed 16 MiB
+ * device array compiled into the library, which every device that loads the library holds
+ * until the process exits.  Limits: N <= 65536 Gaussians and at most 16384 16x16 tiles
+ * (e.g. 2048 x 2048 pixels); larger inputs return CGH_ERR_CAPACITY or
+ * CGH_ERR_UNSUPPORTED_SIZE with a message, and nothing is launched.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  All calls share the one array: calls whose GPU work
+ * overlaps (different streams, or concurrent host threads) race and corrupt each other's
+ * results; order them on one stream. */
+cgh_status cgh_raster_fwd_noalloc(int32_t H, int32_t W, int32_t C, float cutoff,
+                                  const cgh_params* params, void* U_out, void* stream);
+
 /* Backward rasterisation (Suppl. "Detailed Gradient Derivation"): given dU = dL/dU
  * [C][H][W] complex, writes the gradients of all pre-activation parameters.  The
  * Gaussian values are recomputed; no forward state is needed. */

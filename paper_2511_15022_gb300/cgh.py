@@ -48,7 +48,8 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
            "cgh_step", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
-           "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name")
+           "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
+           "cgh_raster_fwd_noalloc")
 
 
 def library_path() -> str:
@@ -79,6 +80,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_plan_status.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32), vp]
     lib.cgh_raster_fwd.argtypes = [vp, ctypes.POINTER(_Params), vp, vp]
+    lib.cgh_raster_fwd_noalloc.argtypes = [i32, i32, i32, f32, ctypes.POINTER(_Params), vp, vp]
     lib.cgh_raster_bwd.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Grads), vp]
     lib.cgh_blasm_fwd.argtypes = [vp, vp, vp, vp]
     lib.cgh_blasm_bwd.argtypes = [vp, vp, vp, vp]
@@ -318,6 +320,28 @@ class Plan:
                              ctypes.c_void_p(loss.data_ptr()), ctypes.byref(gs),
                              ctypes.c_void_p(_stream(stream))), "cgh_step")
         return loss, g
+
+
+def raster_fwd_noalloc(params, H: int, W: int, cutoff: float = 1.0 / 255.0, out=None,
+                       stream=None) -> torch.Tensor:
+    """cgh_raster_fwd_noalloc: the forward raster with no plan and no device allocation
+    inside the library (fixed scratch; N <= 65536, at most 16384 16x16 tiles)."""
+    lib = load()
+    N = int(params["theta"].shape[0])
+    C = int(params["amp"].shape[1])
+    shapes = {"xy_raw": (N, 2), "s_raw": (N, 2), "theta": (N,), "amp": (N, C),
+              "phase": (N, C), "alpha_raw": (N,)}
+    for k in PARAM_KEYS:
+        _need(params[k], torch.float32, shapes[k], k)
+    prm = _Params(N, *[ctypes.c_void_p(params[k].data_ptr()) for k in PARAM_KEYS])
+    U = out if out is not None else torch.empty(C, H, W, dtype=torch.complex64,
+                                                device=params["theta"].device)
+    _need(U, torch.complex64, (C, H, W), "U_out")
+    _check(lib.cgh_raster_fwd_noalloc(int(H), int(W), C, float(cutoff), ctypes.byref(prm),
+                                      ctypes.c_void_p(U.data_ptr()),
+                                      ctypes.c_void_p(_stream(stream))),
+           "cgh_raster_fwd_noalloc")
+    return U
 
 
 def adam_step(groups, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

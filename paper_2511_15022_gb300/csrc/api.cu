@@ -26,6 +26,8 @@ static cgh_status fail(cgh_status st, const char* fmt, ...) {
   return st;
 }
 
+cgh_status cgh_record_error(cgh_status st, const char* msg) { return fail(st, "%s", msg); }
+
 static cgh_status cuda_fail(cudaError_t e, const char* where) {
   return fail(CGH_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -120,6 +120,8 @@ cudaError_t launch_adam(const cgh_adam_group* groups, int n, int step, float b1,
 
 // host-side launch counter (api.cu)
 void cgh_count_launch(int n);
+// record a message for cgh_last_error_string() and return st (api.cu)
+cgh_status cgh_record_error(cgh_status st, const char* msg);
 
 // kernel ids for the event profiler (profile.cu)
 enum KernelId {
