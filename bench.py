@@ -105,6 +105,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_sha() -> str:
+    """Hash of the CUDA sources: ncu traffic figures are valid only for the kernels they
+    were captured from."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2511_15022_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries (lines
+    'traffic-per-launch <kernel> <bytes> sha=<sha>'), or None if absent or stale."""
+    import glob
+    sha = kernel_source_sha()
+    for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(f) as fh:
+            for line in fh:
+                parts = line.strip().strip("`").split()
+                if len(parts) == 4 and parts[0] == "traffic-per-launch" and parts[1] == kernel:
+                    if parts[3] == "sha=" + sha:
+                        return float(parts[2])
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -127,12 +155,12 @@ def oracle_sample(w, params_np, target_np, budget_s: float = 20.0) -> dict:
     from paper_2511_15022_gb300 import inputs
     p64 = {k: v.astype(np.float64) for k, v in params_np.items()}
     HW = w.H * w.W
-    npix = 2000
+    npix = 6000
     idx = inputs.sample_indices(npix, HW, seed=5)
     t0 = time.perf_counter()
     oracle.raster_fwd(p64, w.H, w.W, w.cutoff, pix_idx=idx)
     t_fwd = (time.perf_counter() - t0) * HW / npix
-    ng = 8
+    ng = 48
     sel = inputs.sample_indices(ng, w.N, seed=6)
     dU = inputs.random_field(w.C, w.H, w.W, seed=7).astype(np.complex128)
     t0 = time.perf_counter()
@@ -148,6 +176,60 @@ def oracle_sample(w, params_np, target_np, budget_s: float = 20.0) -> dict:
                        f"propagations; est. {t_step:.1f} s/step")}
 
 
+# ------------------------------------------------------------------ torch / cuFFT baseline
+def torch_blasm_ms(w, dev, steps: int = 10) -> dict:
+    """The paper's comparison class for the propagation stage: BLASM written with PyTorch
+    autograd and cuFFT (centred zero-pad, fft2, band-limited H, ifft2, crop, intensity MSE,
+    backward).  Timed as context only; it is not part of the product path.  H is
+    precomputed outside the timed region."""
+    import math
+
+    import torch
+    C, L, H, W = w.C, w.L, w.H, w.W
+    Ny, Nx = w.pad * H, w.pad * W
+    oy, ox = (Ny - H) // 2, (Nx - W) // 2
+    fy = torch.fft.fftfreq(Ny, d=w.pitch_m, dtype=torch.float64, device=dev)
+    fx = torch.fft.fftfreq(Nx, d=w.pitch_m, dtype=torch.float64, device=dev)
+    Hs = []
+    for l, d in enumerate(w.z_m):
+        row = []
+        for c, lam in enumerate(w.wavelengths_m):
+            fxm = 1.0 / (lam * math.sqrt((2 * d / (Nx * w.pitch_m)) ** 2 + 1))
+            fym = 1.0 / (lam * math.sqrt((2 * d / (Ny * w.pitch_m)) ** 2 + 1))
+            r2 = fx[None, :] ** 2 + fy[:, None] ** 2
+            kz = 2 * math.pi * torch.sqrt(torch.clamp(1 / lam ** 2 - r2, min=0))
+            mask = (fx.abs()[None, :] < fxm) & (fy.abs()[:, None] < fym)
+            row.append(torch.where(mask, torch.exp(1j * kz * d), 0).to(torch.complex64))
+        Hs.append(torch.stack(row))
+    Hst = torch.stack(Hs)  # [L, C, Ny, Nx]
+    g = torch.Generator(device="cpu").manual_seed(5)
+    U0 = (torch.randn(C, H, W, generator=g) + 1j * torch.randn(C, H, W, generator=g)).to(
+        torch.complex64).to(dev).requires_grad_(True)
+    T = torch.rand(L, C, H, W, generator=g).to(dev)
+
+    def once():
+        P = torch.nn.functional.pad(U0, (ox, Nx - W - ox, oy, Ny - H - oy))
+        F = torch.fft.fft2(P)
+        Ud = torch.fft.ifft2(F[None] * Hst)[..., oy:oy + H, ox:ox + W]
+        loss = ((Ud.abs() ** 2 - T) ** 2).mean()
+        loss.backward()
+        U0.grad = None
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.reset_peak_memory_stats(dev)
+    e0.record()
+    for _ in range(steps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    return {"ms_per_step": e0.elapsed_time(e1) / steps,
+            "peak_mem_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
+            "what": "PyTorch autograd + cuFFT BLASM fwd+bwd incl. intensity MSE (no raster)"}
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -157,6 +239,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="autograd", choices=["autograd", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--torch-baseline", action="store_true",
+                    help="also time the PyTorch-autograd + cuFFT propagation stage (context)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -297,8 +381,12 @@ def main():
         roof_k = dominant if dominant in alg else max(fft_kernels, key=lambda k: prof[k]["ms"])
         avg_s = prof[roof_k]["ms"] / prof[roof_k]["launches"] / 1000.0
         achieved = alg[roof_k] / avg_s / 1e9
+        traffic = profiled_traffic(roof_k)
         roofline = {"kernel": roof_k, "bound": "hbm", "achieved": achieved, "peak": peak,
-                    "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                    "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                       "profiles/ (sources sha " + kernel_source_sha() + ")")
+                    if traffic is not None else "no ncu capture of the current kernel sources",
                     "peak_source": f"{peak_kind} HBM copy bandwidth",
                     "algorithmic_bytes_per_launch": alg[roof_k]}
         cpu = None
@@ -320,6 +408,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "kernels": per_kernel, "clocks": clk,
+            "torch_cufft_blasm": torch_blasm_ms(w, dev) if args.torch_baseline else None,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
