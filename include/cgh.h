@@ -209,6 +209,41 @@ typedef struct {
 cgh_status cgh_adam_step(const cgh_adam_group* groups /* host array */, int32_t num_groups,
                          int32_t step, float beta1, float beta2, float eps, void* stream);
 
+/* Adam over any number of parameter groups in one launch: groups_dev is a DEVICE array of
+ * num_groups cgh_adam_group records, offsets_dev a DEVICE array of num_groups + 1 int64
+ * prefix sums of their counts (offsets_dev[num_groups] = total).  Same update as
+ * cgh_adam_step.  Used to step every hologram of a batch at once. */
+cgh_status cgh_adam_step_table(const cgh_adam_group* groups_dev, const int64_t* offsets_dev,
+                               int32_t num_groups, int64_t total, int32_t step, float beta1,
+                               float beta2, float eps, void* stream);
+
+/* Batches of independent holograms (the paper optimises one hologram at a time; batching
+ * many of uneven size is this library's addition).  A batch holds one plan per hologram
+ * (the plans keep their own workspaces and must outlive the batch).  cgh_batch_bind fixes
+ * hologram i's device pointers (parameters, target, device float loss, gradients).
+ * cgh_batch_step runs cgh_step for every hologram: with use_graph = 1 the steps are
+ * captured once (on the first call after a bind) into one CUDA graph with one branch per
+ * hologram and replayed with a single graph launch on `stream`; with use_graph = 0 they are
+ * issued one after another on `stream`.  The bound pointers must stay valid and their
+ * contents are read at replay time.  Profiling (cgh_profile_enable) must be off during the
+ * capturing call.  cgh_batch_kernels_per_step reports the kernels one replay runs. */
+typedef struct cgh_batch cgh_batch;
+cgh_status cgh_batch_create(cgh_plan* const* plans /* host array */, int32_t count,
+                            cgh_batch** out_batch);
+cgh_status cgh_batch_destroy(cgh_batch* batch);
+cgh_status cgh_batch_bind(cgh_batch* batch, int32_t index, const cgh_params* params,
+                          const float* target, float* loss_out, const cgh_grads* grads);
+cgh_status cgh_batch_step(cgh_batch* batch, int32_t use_graph, void* stream);
+int64_t cgh_batch_kernels_per_step(const cgh_batch* batch);
+
+/* Autotuner: runs cgh_step `iters` times (after one warm-up) for every valid combination of
+ * column block {1,2,4,8} x row block {1,2,3,4,8} x FFT kernel family {specialised, generic}
+ * on the given data, keeps the fastest on the plan and writes it to best_out (may be NULL).
+ * Gradients and loss_out are overwritten. */
+cgh_status cgh_autotune(cgh_plan* plan, const cgh_params* params, const float* target,
+                        const cgh_grads* grads, float* loss_out, int32_t iters, void* stream,
+                        cgh_tuning* best_out);
+
 /* Number of kernels launched by this thread's calls into the library so far (host
  * counter; used to report launches per step). */
 int64_t cgh_launch_count(void);

@@ -49,7 +49,9 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
            "cgh_step", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
            "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
-           "cgh_raster_fwd_noalloc")
+           "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
+           "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
+           "cgh_autotune")
 
 
 def library_path() -> str:
@@ -88,6 +90,15 @@ def load(build_if_missing: bool = True):
     lib.cgh_forward_loss.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp]
     lib.cgh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads), vp]
     lib.cgh_adam_step.argtypes = [ctypes.POINTER(_AdamGroup), i32, i32, f32, f32, f32, vp]
+    lib.cgh_adam_step_table.argtypes = [vp, vp, i32, i64, i32, f32, f32, f32, vp]
+    lib.cgh_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+    lib.cgh_batch_destroy.argtypes = [vp]
+    lib.cgh_batch_bind.argtypes = [vp, i32, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads)]
+    lib.cgh_batch_step.argtypes = [vp, i32, vp]
+    lib.cgh_batch_kernels_per_step.argtypes = [vp]
+    lib.cgh_batch_kernels_per_step.restype = i64
+    lib.cgh_autotune.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Grads), vp, i32,
+                                 vp, ctypes.POINTER(_Tuning)]
     lib.cgh_launch_count.restype = i64
     lib.cgh_last_error_string.restype = ctypes.c_char_p
     lib.cgh_profile_enable.argtypes = [i32]
@@ -97,7 +108,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("cgh_launch_count", "cgh_last_error_string", "cgh_kernel_count",
-                        "cgh_kernel_name"):
+                        "cgh_kernel_name", "cgh_batch_kernels_per_step"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -308,6 +319,20 @@ class Plan:
                                      ctypes.c_void_p(_stream(stream))), "cgh_forward_loss")
         return loss
 
+    def autotune(self, params, target, iters: int = 5, stream=None) -> dict:
+        """cgh_autotune: time every valid block shape on this data and keep the fastest."""
+        prm = self._params(params)
+        _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
+        g = self.empty_grads(prm.N)
+        gs = self._grads(g, prm.N)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        best = _Tuning()
+        _check(_lib.cgh_autotune(self._h, ctypes.byref(prm), ctypes.c_void_p(target.data_ptr()),
+                                 ctypes.byref(gs), ctypes.c_void_p(loss.data_ptr()), int(iters),
+                                 ctypes.c_void_p(_stream(stream)), ctypes.byref(best)),
+               "cgh_autotune")
+        return {k: getattr(best, k) for k, _ in _Tuning._fields_}
+
     def step(self, params, target, grads=None, loss_out=None, stream=None):
         """Fused forward + backward (cgh_step).  Returns (loss[1], grads)."""
         prm = self._params(params)
@@ -340,7 +365,9 @@ def raster_fwd_noalloc(params, H: int, W: int, cutoff: float = 1.0 / 255.0, out=
     _check(lib.cgh_raster_fwd_noalloc(int(H), int(W), C, float(cutoff), ctypes.byref(prm),
                                       ctypes.c_void_p(U.data_ptr()),
                                       ctypes.c_void_p(_stream(stream))),
-           "cgh_raster_fwd_noalloc")
+           "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
+           "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
+           "cgh_autotune")
     return U
 
 
@@ -355,3 +382,79 @@ def adam_step(groups, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
                             float(lr))
     _check(lib.cgh_adam_step(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
                              ctypes.c_void_p(_stream(stream))), "cgh_adam_step")
+
+
+class AdamTable:
+    """Adam over many parameter groups in one launch (cgh_adam_step_table).  groups is a
+    list of (param, exp_avg, exp_avg_sq, grad, lr); the tensors must stay alive."""
+
+    def __init__(self, groups, beta1=0.9, beta2=0.999, eps=1e-8):
+        load()
+        self.groups = list(groups)
+        dev = self.groups[0][0].device
+        recs = (_AdamGroup * len(self.groups))()
+        offs = [0]
+        for i, (p, m, v, g, lr) in enumerate(self.groups):
+            for t, name in ((m, "exp_avg"), (v, "exp_avg_sq"), (g, "grad")):
+                _need(t, torch.float32, tuple(p.shape), name)
+            recs[i] = _AdamGroup(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                 p.numel(), float(lr))
+            offs.append(offs[-1] + p.numel())
+        raw = bytes(recs)
+        self.table = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(dev)
+        self.offsets = torch.tensor(offs, dtype=torch.int64, device=dev)
+        self.total = offs[-1]
+        self.beta1, self.beta2, self.eps = beta1, beta2, eps
+        self.t = 0
+
+    def step(self, stream=None):
+        self.t += 1
+        _check(_lib.cgh_adam_step_table(ctypes.c_void_p(self.table.data_ptr()),
+                                        ctypes.c_void_p(self.offsets.data_ptr()),
+                                        len(self.groups), self.total, self.t, self.beta1,
+                                        self.beta2, self.eps, ctypes.c_void_p(_stream(stream))),
+               "cgh_adam_step_table")
+
+
+class Batch:
+    """Independent holograms stepped together (cgh_batch_*): one graph launch per step."""
+
+    def __init__(self, plans):
+        load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(_lib.cgh_batch_create(arr, len(self.plans), ctypes.byref(h)), "cgh_batch_create")
+        self._h = h
+        self._keep = {}
+
+    def bind(self, i: int, params, target, grads, loss_out):
+        plan = self.plans[i]
+        prm = plan._params(params)
+        gs = plan._grads(grads, prm.N)
+        _need(target, torch.float32, (plan.L, plan.C, plan.H, plan.W), "target")
+        _need(loss_out, torch.float32, (1,), "loss_out")
+        self._keep[i] = (params, target, grads, loss_out)
+        _check(_lib.cgh_batch_bind(self._h, int(i), ctypes.byref(prm),
+                                   ctypes.c_void_p(target.data_ptr()),
+                                   ctypes.c_void_p(loss_out.data_ptr()), ctypes.byref(gs)),
+               "cgh_batch_bind")
+
+    def step(self, use_graph: bool = True, stream=None):
+        _check(_lib.cgh_batch_step(self._h, 1 if use_graph else 0,
+                                   ctypes.c_void_p(_stream(stream))), "cgh_batch_step")
+
+    @property
+    def kernels_per_step(self) -> int:
+        return int(_lib.cgh_batch_kernels_per_step(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.cgh_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -39,3 +39,7 @@ bool spec_rows_b(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecR
                  cudaStream_t s, cudaError_t* err, bool dry);
 bool spec_cols_b(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
                  cudaStream_t s, cudaError_t* err, bool dry);
+bool spec_rows_c(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRowArgs* a,
+                 cudaStream_t s, cudaError_t* err, bool dry);
+bool spec_cols_c(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
+                 cudaStream_t s, cudaError_t* err, bool dry);
