@@ -29,10 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd iterations/sec at 1080p x3 planes"
 UNIT = "it/s"
 
-# Adam learning rates per parameter group (Sec. 4; positions use the start of the cosine
-# schedule)
-LRS = {"xy_raw": 1e-2, "s_raw": 5e-3, "theta": 1e-3, "amp": 2.5e-3, "phase": 2.5e-3,
-       "alpha_raw": 2.5e-2}
+from paper_2511_15022_gb300.optim import LRS  # noqa: E402  (Adam rates per group, Sec. 4)
 
 
 def algorithmic_bytes(w) -> dict:
@@ -357,6 +354,95 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 1000, check_ever
                        "intensities")}
 
 
+# ------------------------------------------------------------------ learned initialiser
+def learned_init_bench(dev, full: bool = False) -> dict:
+    """The learned-initialiser workload: planted 512 x 512 RGB targets on one plane at 5 mm,
+    16,384 Gaussians each (32 x 32 cells x 16).  Training pairs come from the plain
+    optimiser (anchor initialisation, the paper's Adam rates) run through the batched
+    graph; the encoder trains on the GPU through the library's BF16 convolutions and the
+    raster + BLASM backward; held-out targets are then refined from each initialisation.
+    `full`: 2000 targets (1800 / 200), 300 generation iterations, 2000 training steps;
+    otherwise a bounded 400-target copy (350 / 50, 200 iterations, 1000 steps)."""
+    import torch
+
+    from paper_2511_15022_gb300 import encoder as E
+    count, n_eval, gen_iters, steps = (2000, 200, 300, 2000) if full else (400, 50, 200, 1000)
+    iters, warmup = 200, 20
+    H = W = 512
+    wl, pitch, z = (638e-9, 520e-9, 450e-9), 8e-6, 5e-3
+    t0 = time.perf_counter()
+    T = E.planted_targets(count, H, W, wl, pitch, z, n_planted=16384, seed=100000, device=dev)
+    torch.cuda.synchronize()
+    t_targets = time.perf_counter() - t0
+    ntr = count - n_eval
+    pipe = E.Pipeline(H, W, wl, pitch, z, chunk=50, train_batch=16, device=dev, seed=0)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1000.0
+
+    (data, gen_hist), t_gen = timed(lambda: pipe.generate(T[:ntr], gen_iters))
+    log, t_train = timed(lambda: pipe.train(T[:ntr], data, steps, param_weight=1.0,
+                                            log_every=max(1, steps // 4)))
+    ev = T[ntr:]
+    init_l, t_pred = timed(lambda: pipe.predict(ev))
+
+    def curve(hist):
+        db = E.psnr_db(hist)
+        at = {str(c): round(float(db[:, c].mean()), 2) for c in (0, 10, 25, 50, 100, 150, 200)}
+        to = {}
+        for lvl in (24, 25, 26):
+            its = E.iterations_to(db, lvl)
+            ok = sorted(v for v in its if v is not None)
+            # median with unreached targets counted as beyond the run
+            med = ok[len(its) // 2] if len(ok) > len(its) // 2 else None
+            to[str(lvl)] = {"reached": len(ok), "of": len(its), "median_iters": med}
+        return {"psnr_db_at_iter": at, "iters_to_db": to}, db.mean(0)
+
+    runs = {
+        "plain_random_init": (pipe.random_init(n_eval, 7), 0),
+        "random_init_warmup": (pipe.random_init(n_eval, 7), warmup),
+        "anchor_init_warmup": (pipe.enc.anchors(n_eval, H, W), warmup),
+        "learned_init_warmup": (init_l, warmup),
+    }
+    refine, means = {}, {}
+    for name, (init, wu) in runs.items():
+        _, h = pipe.refine(init, ev, iters, warmup=wu)
+        refine[name], means[name] = curve(h)
+    plain_final = float(means["plain_random_init"][-1])
+    ok = (means["learned_init_warmup"] >= plain_final).nonzero()
+    reach = int(ok[0]) if ok.numel() else None
+    gen_db = E.psnr_db(gen_hist)
+    pipe.close()
+    return {
+        "workload": "512x512 RGB 638/520/450 nm, 8 um pitch, 1 plane at 5 mm, 16384 Gaussians "
+                    "(32x32 cells x 16 slots), planted structured targets, mean intensity 0.35",
+        "protocol": "full" if full else "bounded copy",
+        "targets": count, "train": ntr, "held_out": n_eval,
+        "target_synthesis_s": round(t_targets, 2),
+        "data_generation": {"iterations": gen_iters, "seconds": round(t_gen, 2),
+                            "hologram_iterations_per_s": round(ntr * gen_iters / t_gen, 1),
+                            "final_psnr_db_mean": round(float(gen_db[:, -1].mean()), 2)},
+        "training": {"steps": steps, "batch": 16, "seconds": round(t_train, 2),
+                     "images_per_s": round(steps * 16 / t_train, 1),
+                     "log_step_intensity_loss_param_term": [(i, round(a, 5), round(b, 4))
+                                                             for i, a, b in log]},
+        "inference_ms_per_image": round(1000.0 * t_pred / n_eval, 3),
+        "refinement_iters": iters, "warmup_iters": warmup,
+        "refinement": refine,
+        "learned_reaches_plain_final_psnr_at_iter": reach,
+        "plain_final_psnr_db": round(plain_final, 2),
+        "psnr": "10 log10(1 / intensity MSE) from the step's own loss, targets in [0, 1]",
+        "note": "no initialisation reaches 30 dB within 200 iterations on these targets; "
+                "the 24 / 25 / 26 dB levels are reported instead",
+    }
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -367,6 +453,8 @@ def main():
     ap.add_argument("--mode", default="autograd", choices=["autograd", "fused"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--learned-full", action="store_true",
+                    help="run the learned-initialiser extra on all 2000 targets")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-holograms and time-to-PSNR measurements")
     ap.add_argument("--torch-baseline", action="store_true",
@@ -547,6 +635,7 @@ def main():
         if not args.no_extras and world == 1:
             line["batched"] = batched_bench(dev, steps=max(5, args.steps // 4), warmup=3)
             line["time_to_psnr"] = time_to_psnr(dev, plan_tuning=tuned)
+            line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

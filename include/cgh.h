@@ -212,10 +212,12 @@ cgh_status cgh_adam_step(const cgh_adam_group* groups /* host array */, int32_t 
 /* Adam over any number of parameter groups in one launch: groups_dev is a DEVICE array of
  * num_groups cgh_adam_group records, offsets_dev a DEVICE array of num_groups + 1 int64
  * prefix sums of their counts (offsets_dev[num_groups] = total).  Same update as
- * cgh_adam_step.  Used to step every hologram of a batch at once. */
+ * cgh_adam_step with every group's learning rate multiplied by lr_scale >= 0 (a schedule
+ * shared by all groups; 0 leaves everything untouched).  Used to step every hologram of a
+ * batch at once. */
 cgh_status cgh_adam_step_table(const cgh_adam_group* groups_dev, const int64_t* offsets_dev,
                                int32_t num_groups, int64_t total, int32_t step, float beta1,
-                               float beta2, float eps, void* stream);
+                               float beta2, float eps, float lr_scale, void* stream);
 
 /* Batches of independent holograms (the paper optimises one hologram at a time; batching
  * many of uneven size is this library's addition).  A batch holds one plan per hologram
@@ -243,6 +245,54 @@ int64_t cgh_batch_kernels_per_step(const cgh_batch* batch);
 cgh_status cgh_autotune(cgh_plan* plan, const cgh_params* params, const float* target,
                         const cgh_grads* grads, float* loss_out, int32_t iters, void* stream,
                         cgh_tuning* best_out);
+
+/* ---- learned initialiser (the paper has no learned part; it lists feed-forward prediction
+ * as future work, Sec. 6): a stack of 3x3 convolutions with BF16 weights and activations
+ * (16-bit bfloat16 values passed as void*) and FP32 accumulation, and the decode from the
+ * last layer to Gaussian parameters.
+ *
+ * cgh_conv3x3_fwd: y[b][co][oy][ox] = act(bias[co] + sum_{ci,ky,kx} w[co][ci][ky][kx]
+ *   x[b][ci][oy*stride+ky-1][ox*stride+kx-1]) (zero outside the image), act = ReLU if relu.
+ *   x: [B][CI][Hi][Wi] bf16; w: [CO][CI][3][3] bf16; bias: [CO] f32; y: [B][CO][Ho][Wo] with
+ *   Ho = (Hi-1)/stride + 1, bf16 or f32 (y_f32).  CI <= 170. */
+cgh_status cgh_conv3x3_fwd(int32_t B, int32_t CI, int32_t Hi, int32_t Wi, int32_t CO,
+                           int32_t stride, const void* x, const void* w, const float* bias,
+                           int32_t relu, void* y, int32_t y_f32, void* stream);
+
+/* Backward of cgh_conv3x3_fwd given dy = dL/dy (f32, same layout as y) and the forward
+ * output y (needed for the ReLU mask when relu = 1): dx = dL/dx (f32, may be NULL to skip),
+ * dw = dL/dw [CO][CI][3][3] f32 and db = dL/dbias [CO] f32 (both overwritten).  CO <= 340. */
+cgh_status cgh_conv3x3_bwd(int32_t B, int32_t CI, int32_t Hi, int32_t Wi, int32_t CO,
+                           int32_t stride, const void* x, const void* w, int32_t relu,
+                           const void* y, int32_t y_f32, const float* dy, float* dx, float* dw,
+                           float* db, void* stream);
+
+/* dst[i] = bf16(src[i]) (round to nearest even), n elements. */
+cgh_status cgh_cast_bf16(int64_t n, const float* src, void* dst, void* stream);
+
+/* Decode the encoder output out [B][S*P][CY][CX] f32 (P = 6 + 2C channels per slot: dx, dy,
+ * sx, sy, theta, amp[C], phase[C], alpha) into pre-activation parameters of B images of
+ * N = CY*CX*S Gaussians each (arrays of B*N records, layouts as cgh_params; written through
+ * a cgh_grads struct of writable pointers).  Gaussian n = (cy*CX + cx)*S + g sits at slot g
+ * of cell (cy, cx), slots on a ceil(sqrt(S))^2 grid inside the cell (cells of W/CX x H/CY
+ * pixels); parameter = base + scale * out with base = the slot's centre (pre-activation,
+ * atanh(2 x / W - 1)) for the position and log(1.5), 0, 0.5, 0, -0.5 for scale, rotation,
+ * amplitude, phase, opacity; scales 0.02 (position), 0.5 (scale), 1, 0.5 (amplitude), 1, 1.
+ * Decoding zeros gives the plain structured initialisation. */
+cgh_status cgh_encoder_decode(int32_t B, int32_t CY, int32_t CX, int32_t S, int32_t C, int32_t H,
+                              int32_t W, const float* out, const cgh_grads* params_out,
+                              void* stream);
+
+/* Weighted squared-error term of the encoder's training loss: grad[i] = 2 w (pred[i] -
+ * target[i]), added to grad[i] when accumulate = 1 (overwriting it when 0), and, if
+ * loss_accum (device float) is not NULL, *loss_accum += w sum_i (pred[i] - target[i])^2. */
+cgh_status cgh_mse_grad(int64_t n, const float* pred, const float* target, float weight,
+                        int32_t accumulate, float* grad, float* loss_accum, void* stream);
+
+/* Adjoint of the decode: dout = scale * dL/dparameter (dout overwritten). */
+cgh_status cgh_encoder_decode_bwd(int32_t B, int32_t CY, int32_t CX, int32_t S, int32_t C,
+                                  int32_t H, int32_t W, const cgh_grads* param_grads,
+                                  float* dout, void* stream);
 
 /* Number of kernels launched by this thread's calls into the library so far (host
  * counter; used to report launches per step). */

@@ -81,3 +81,20 @@ def decode(out, S: int, C: int, H: int, W: int):
             "alpha_raw": ALPHA_BASE + ob[:, 5 + 2 * C],
         })
     return res
+
+
+def decode_bwd(grads, S: int, C: int, CY: int, CX: int):
+    """Adjoint of decode: per-image gradient dicts w.r.t. the decoded parameters ->
+    dL/d(encoder output) [B, S*P, CY, CX].  The decode is affine, so each output channel's
+    gradient is its parameter's gradient times the channel's scale."""
+    P = 6 + 2 * C
+    B = len(grads)
+    o = np.zeros((B, CY * CX * S, P))
+    for b, g in enumerate(grads):
+        o[b, :, 0:2] = POS_SCALE * np.asarray(g["xy_raw"], np.float64)
+        o[b, :, 2:4] = SCALE_SCALE * np.asarray(g["s_raw"], np.float64)
+        o[b, :, 4] = np.asarray(g["theta"], np.float64)
+        o[b, :, 5:5 + C] = AMP_SCALE * np.asarray(g["amp"], np.float64)
+        o[b, :, 5 + C:5 + 2 * C] = np.asarray(g["phase"], np.float64)
+        o[b, :, 5 + 2 * C] = np.asarray(g["alpha_raw"], np.float64)
+    return o.reshape(B, CY, CX, S, P).transpose(0, 3, 4, 1, 2).reshape(B, S * P, CY, CX)

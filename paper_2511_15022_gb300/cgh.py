@@ -51,7 +51,8 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
            "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
-           "cgh_autotune")
+           "cgh_autotune", "cgh_conv3x3_fwd", "cgh_conv3x3_bwd", "cgh_cast_bf16",
+           "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad")
 
 
 def library_path() -> str:
@@ -90,7 +91,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_forward_loss.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp]
     lib.cgh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads), vp]
     lib.cgh_adam_step.argtypes = [ctypes.POINTER(_AdamGroup), i32, i32, f32, f32, f32, vp]
-    lib.cgh_adam_step_table.argtypes = [vp, vp, i32, i64, i32, f32, f32, f32, vp]
+    lib.cgh_adam_step_table.argtypes = [vp, vp, i32, i64, i32, f32, f32, f32, f32, vp]
     lib.cgh_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     lib.cgh_batch_destroy.argtypes = [vp]
     lib.cgh_batch_bind.argtypes = [vp, i32, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads)]
@@ -99,6 +100,15 @@ def load(build_if_missing: bool = True):
     lib.cgh_batch_kernels_per_step.restype = i64
     lib.cgh_autotune.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Grads), vp, i32,
                                  vp, ctypes.POINTER(_Tuning)]
+    lib.cgh_conv3x3_fwd.argtypes = [i32, i32, i32, i32, i32, i32, vp, vp, vp, i32, vp, i32, vp]
+    lib.cgh_conv3x3_bwd.argtypes = [i32, i32, i32, i32, i32, i32, vp, vp, i32, vp, i32, vp, vp,
+                                    vp, vp, vp]
+    lib.cgh_cast_bf16.argtypes = [i64, vp, vp, vp]
+    lib.cgh_encoder_decode.argtypes = [i32, i32, i32, i32, i32, i32, i32, vp,
+                                       ctypes.POINTER(_Grads), vp]
+    lib.cgh_encoder_decode_bwd.argtypes = [i32, i32, i32, i32, i32, i32, i32,
+                                           ctypes.POINTER(_Grads), vp, vp]
+    lib.cgh_mse_grad.argtypes = [i64, vp, vp, f32, i32, vp, vp, vp]
     lib.cgh_launch_count.restype = i64
     lib.cgh_last_error_string.restype = ctypes.c_char_p
     lib.cgh_profile_enable.argtypes = [i32]
@@ -365,9 +375,7 @@ def raster_fwd_noalloc(params, H: int, W: int, cutoff: float = 1.0 / 255.0, out=
     _check(lib.cgh_raster_fwd_noalloc(int(H), int(W), C, float(cutoff), ctypes.byref(prm),
                                       ctypes.c_void_p(U.data_ptr()),
                                       ctypes.c_void_p(_stream(stream))),
-           "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
-           "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
-           "cgh_autotune")
+           "cgh_raster_fwd_noalloc")
     return U
 
 
@@ -407,12 +415,14 @@ class AdamTable:
         self.beta1, self.beta2, self.eps = beta1, beta2, eps
         self.t = 0
 
-    def step(self, stream=None):
+    def step(self, lr_scale: float = 1.0, stream=None):
+        """One Adam step of every group, learning rates multiplied by lr_scale."""
         self.t += 1
         _check(_lib.cgh_adam_step_table(ctypes.c_void_p(self.table.data_ptr()),
                                         ctypes.c_void_p(self.offsets.data_ptr()),
                                         len(self.groups), self.total, self.t, self.beta1,
-                                        self.beta2, self.eps, ctypes.c_void_p(_stream(stream))),
+                                        self.beta2, self.eps, float(lr_scale),
+                                        ctypes.c_void_p(_stream(stream))),
                "cgh_adam_step_table")
 
 
@@ -458,3 +468,136 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- learned-initialiser layers
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def conv_out_size(n: int, stride: int) -> int:
+    return (n - 1) // stride + 1
+
+
+def conv3x3_fwd(x_bf16, w_bf16, bias, stride: int, relu: bool, out_f32: bool = False,
+                out=None, stream=None):
+    """cgh_conv3x3_fwd.  x [B,CI,H,W] bf16, w [CO,CI,3,3] bf16, bias [CO] f32."""
+    lib = load()
+    B, CI, H, W = x_bf16.shape
+    CO = w_bf16.shape[0]
+    Ho, Wo = conv_out_size(H, stride), conv_out_size(W, stride)
+    _need(x_bf16, torch.bfloat16, (B, CI, H, W), "x")
+    _need(w_bf16, torch.bfloat16, (CO, CI, 3, 3), "w")
+    _need(bias, torch.float32, (CO,), "bias")
+    ydt = torch.float32 if out_f32 else torch.bfloat16
+    y = out if out is not None else torch.empty(B, CO, Ho, Wo, device=x_bf16.device, dtype=ydt)
+    _need(y, ydt, (B, CO, Ho, Wo), "y")
+    _check(lib.cgh_conv3x3_fwd(B, CI, H, W, CO, stride, _ptr(x_bf16), _ptr(w_bf16), _ptr(bias),
+                               1 if relu else 0, _ptr(y), 1 if out_f32 else 0,
+                               ctypes.c_void_p(_stream(stream))), "cgh_conv3x3_fwd")
+    return y
+
+
+def conv3x3_bwd(x_bf16, w_bf16, y, dy, stride: int, relu: bool, want_dx: bool = True,
+                dx=None, dw=None, db=None, stream=None):
+    """cgh_conv3x3_bwd: returns (dx or None, dw, db), all f32 (dw, db overwritten)."""
+    lib = load()
+    B, CI, H, W = x_bf16.shape
+    CO = w_bf16.shape[0]
+    dev = x_bf16.device
+    if want_dx and dx is None:
+        dx = torch.empty(B, CI, H, W, device=dev)
+    if not want_dx:
+        dx = None
+    dw = dw if dw is not None else torch.empty(CO, CI, 3, 3, device=dev)
+    db = db if db is not None else torch.empty(CO, device=dev)
+    _need(x_bf16, torch.bfloat16, (B, CI, H, W), "x")
+    _need(w_bf16, torch.bfloat16, (CO, CI, 3, 3), "w")
+    yshape = (B, CO, conv_out_size(H, stride), conv_out_size(W, stride))
+    if y is not None:
+        _need(y, y.dtype, yshape, "y")
+        if y.dtype not in (torch.float32, torch.bfloat16):
+            raise CGHError("y must be float32 or bfloat16")
+    elif relu:
+        raise CGHError("relu backward needs the forward output y")
+    _need(dy, torch.float32, yshape, "dy")
+    if dx is not None:
+        _need(dx, torch.float32, (B, CI, H, W), "dx")
+    _need(dw, torch.float32, (CO, CI, 3, 3), "dw")
+    _need(db, torch.float32, (CO,), "db")
+    y_f32 = 1 if (y is not None and y.dtype == torch.float32) else 0
+    _check(lib.cgh_conv3x3_bwd(B, CI, H, W, CO, stride, _ptr(x_bf16), _ptr(w_bf16),
+                               1 if relu else 0, _ptr(y), y_f32, _ptr(dy), _ptr(dx), _ptr(dw),
+                               _ptr(db), ctypes.c_void_p(_stream(stream))), "cgh_conv3x3_bwd")
+    return dx, dw, db
+
+
+def cast_bf16(src, dst=None, stream=None):
+    """cgh_cast_bf16: f32 -> bf16 (round to nearest even)."""
+    lib = load()
+    if not src.is_cuda or src.dtype != torch.float32 or not src.is_contiguous():
+        raise CGHError("src must be a contiguous CUDA float32 tensor")
+    d = dst if dst is not None else torch.empty(src.shape, dtype=torch.bfloat16, device=src.device)
+    _need(d, torch.bfloat16, tuple(src.shape), "dst")
+    _check(lib.cgh_cast_bf16(src.numel(), _ptr(src), _ptr(d), ctypes.c_void_p(_stream(stream))),
+           "cgh_cast_bf16")
+    return d
+
+
+def param_dict(n: int, C: int, device) -> Dict[str, torch.Tensor]:
+    """Empty pre-activation parameter (or gradient) arrays for n Gaussians."""
+    return {"xy_raw": torch.empty(n, 2, device=device), "s_raw": torch.empty(n, 2, device=device),
+            "theta": torch.empty(n, device=device), "amp": torch.empty(n, C, device=device),
+            "phase": torch.empty(n, C, device=device), "alpha_raw": torch.empty(n, device=device)}
+
+
+def _param_struct(d, n: int, C: int):
+    shapes = {"xy_raw": (n, 2), "s_raw": (n, 2), "theta": (n,), "amp": (n, C), "phase": (n, C),
+              "alpha_raw": (n,)}
+    for k in PARAM_KEYS:
+        _need(d[k], torch.float32, shapes[k], k)
+    return _Grads(*[_ptr(d[k]) for k in PARAM_KEYS])
+
+
+def encoder_decode(out, S: int, C: int, H: int, W: int, params=None, stream=None):
+    """cgh_encoder_decode: out [B, S*(6+2C), CY, CX] f32 -> parameters of B*CY*CX*S Gaussians."""
+    lib = load()
+    B, P, CY, CX = out.shape
+    if P != S * (6 + 2 * C):
+        raise CGHError(f"encoder output has {P} channels, expected {S * (6 + 2 * C)}")
+    _need(out, torch.float32, (B, P, CY, CX), "out")
+    n = B * CY * CX * S
+    p = params if params is not None else param_dict(n, C, out.device)
+    st = _param_struct(p, n, C)
+    _check(lib.cgh_encoder_decode(B, CY, CX, S, C, H, W, _ptr(out), ctypes.byref(st),
+                                  ctypes.c_void_p(_stream(stream))), "cgh_encoder_decode")
+    return p
+
+
+def encoder_decode_bwd(grads, B: int, CY: int, CX: int, S: int, C: int, H: int, W: int,
+                       dout=None, stream=None):
+    """cgh_encoder_decode_bwd: parameter gradients -> dL/d(encoder output)."""
+    lib = load()
+    dev = grads["theta"].device
+    shape = (B, S * (6 + 2 * C), CY, CX)
+    dout = dout if dout is not None else torch.empty(shape, device=dev)
+    _need(dout, torch.float32, shape, "dout")
+    st = _param_struct(grads, B * CY * CX * S, C)
+    _check(lib.cgh_encoder_decode_bwd(B, CY, CX, S, C, H, W, ctypes.byref(st), _ptr(dout),
+                                      ctypes.c_void_p(_stream(stream))), "cgh_encoder_decode_bwd")
+    return dout
+
+
+def mse_grad(pred, target, weight: float, grad_out, accumulate: bool = False, loss_accum=None,
+             stream=None):
+    """cgh_mse_grad: grad_out (+)= 2 w (pred - target); loss_accum += w sum (pred - target)^2."""
+    lib = load()
+    for t, name in ((pred, "pred"), (target, "target"), (grad_out, "grad")):
+        _need(t, torch.float32, tuple(pred.shape), name)
+        if not t.is_contiguous():
+            raise CGHError(f"{name} must be contiguous")
+    if loss_accum is not None:
+        _need(loss_accum, torch.float32, (1,), "loss_accum")
+    _check(lib.cgh_mse_grad(pred.numel(), _ptr(pred), _ptr(target), float(weight),
+                            1 if accumulate else 0, _ptr(grad_out), _ptr(loss_accum),
+                            ctypes.c_void_p(_stream(stream))), "cgh_mse_grad")

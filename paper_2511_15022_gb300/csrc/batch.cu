@@ -241,10 +241,12 @@ __global__ void k_adam_table(const cgh_adam_group* __restrict__ groups,
 extern "C" cgh_status cgh_adam_step_table(const cgh_adam_group* groups_dev,
                                           const int64_t* offsets_dev, int32_t num_groups,
                                           int64_t total, int32_t step, float beta1,
-                                          float beta2, float eps, void* stream) {
-  if (!groups_dev || !offsets_dev || num_groups < 1 || total < 0 || step < 1)
+                                          float beta2, float eps, float lr_scale, void* stream) {
+  if (!groups_dev || !offsets_dev || num_groups < 1 || total < 0 || step < 1 || !(lr_scale >= 0.f))
     return cgh_record_error(CGH_ERR_ARG, "bad Adam table arguments");
-  const double bc1 = 1.0 - pow((double)beta1, (double)step);
+  // the learning-rate scale is folded into the first-moment bias correction (lr / bc1)
+  const double bc1 = (1.0 - pow((double)beta1, (double)step)) / (lr_scale > 0.f ? lr_scale : 1.0);
+  if (lr_scale == 0.f) return CGH_OK;
   const double bc2 = 1.0 - pow((double)beta2, (double)step);
   if (total == 0) return CGH_OK;
   long long blocks = (total + 255) / 256;

@@ -128,7 +128,7 @@ enum KernelId {
   KID_PREPROCESS = 0, KID_SCAN_TILES, KID_EMIT, KID_RASTER_FWD, KID_RASTER_BWD,
   KID_GRAD_FINALIZE, KID_ROWS_PAD_FWD, KID_COLS_FWD_PLANES, KID_ROWS_LOSS,
   KID_COLS_BWD_PLANES, KID_ROWS_INV_CROP, KID_LOSS_POINTWISE, KID_LOSS_FINALIZE, KID_ADAM,
-  KID_COUNT
+  KID_ENCODER, KID_COUNT
 };
 // Bracket one kernel launch: records a CUDA event before and after it on its stream when
 // profiling is enabled; otherwise only the launch counter moves.

@@ -156,3 +156,29 @@ def sample_indices(count: int, total: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     count = min(count, total)
     return np.sort(rng.choice(total, size=count, replace=False)).astype(np.int64)
+
+
+def planted_scene(N: int, C: int, H: int, W: int, seed: int, blobs: int = 8,
+                  dtype=np.float32) -> dict:
+    """Pre-activation parameters of a structured planted scene: gaussian_params draws with
+    every phase zero and each channel's amplitude read from a smooth field (a sum of
+    `blobs` isotropic Gaussian blobs, sigma U(H/24, H/6), peak U(0.3, 1), normalised to
+    maximum 1) at the Gaussian's mean.  A random-phase scene would render as speckle; this
+    one renders as an image-like intensity that the scene's own parameters reproduce."""
+    p = gaussian_params(N, C, H, W, seed, dtype=np.float64)
+    rng = np.random.default_rng(seed ^ 0x5EED)
+    x = (np.tanh(p["xy_raw"][:, 0]) + 1.0) / 2.0 * W
+    y = (np.tanh(p["xy_raw"][:, 1]) + 1.0) / 2.0 * H
+    amp = np.zeros((N, C))
+    for c in range(C):
+        for _ in range(blobs):
+            cx, cy = rng.uniform(0, W), rng.uniform(0, H)
+            sig = rng.uniform(H / 24.0, H / 6.0)
+            amp[:, c] += rng.uniform(0.3, 1.0) * np.exp(-((x - cx) ** 2 + (y - cy) ** 2)
+                                                        / (2.0 * sig * sig))
+        m = amp[:, c].max()
+        if m > 0:
+            amp[:, c] /= m
+    p["amp"] = amp
+    p["phase"] = np.zeros((N, C))
+    return {k: np.ascontiguousarray(v.astype(dtype)) for k, v in p.items()}

@@ -59,3 +59,17 @@ def test_decode_zero_output_is_the_anchor_grid():
     assert len(x) == 4 * 6 * 16
     assert np.allclose(np.exp(p["s_raw"]) + 0.1, 1.6)
     assert np.all(p["phase"] == 0) and np.allclose(p["amp"], 0.5) and np.allclose(p["alpha_raw"], -0.5)
+
+
+def test_decode_bwd_is_the_adjoint():
+    """<decode(out + e) - decode(out), g> = <e, decode_bwd(g)> for random out, e, g: the decode
+    is affine, so the identity is exact up to rounding for any step e."""
+    S, C, H, W, CY, CX = 9, 2, 40, 48, 2, 3
+    rng = np.random.default_rng(11)
+    out = rng.standard_normal((2, S * (6 + 2 * C), CY, CX))
+    e = rng.standard_normal(out.shape)
+    p0, p1 = er.decode(out, S, C, H, W), er.decode(out + e, S, C, H, W)
+    g = [{k: rng.standard_normal(np.shape(v)) for k, v in d.items()} for d in p0]
+    lhs = sum(float(np.sum((p1[b][k] - p0[b][k]) * g[b][k])) for b in range(2) for k in g[b])
+    rhs = float(np.sum(e * er.decode_bwd(g, S, C, CY, CX)))
+    assert abs(lhs - rhs) < 1e-9 * max(1.0, abs(lhs))

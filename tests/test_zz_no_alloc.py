@@ -58,3 +58,16 @@ def test_noalloc_refuses_inputs_beyond_its_scratch(dev):
     st = lib.cgh_raster_fwd_noalloc(4096, 4096, 1, 1 / 255, ctypes.byref(prm),
                                     ctypes.c_void_p(out.data_ptr()), None)
     assert st == 5 and b"16384" in lib.cgh_last_error_string()
+
+
+def test_noalloc_python_binding(dev):
+    """The binding of the same name marshals to the C entry point and reports its errors."""
+    from paper_2511_15022_gb300 import cgh
+    w = inputs.custom(40, 60, 200, z_m=(0.0,), seed=72)
+    p = to_dev(inputs.params_for(w), dev)
+    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
+                    max_gaussians=w.N, device=dev)
+    U = cgh.raster_fwd_noalloc(p, w.H, w.W, w.cutoff)
+    assert rel_l2(c64(U), c64(plan.raster_fwd(p))) < FIELD_TOL
+    with pytest.raises(cgh.CGHError, match="16384"):
+        cgh.raster_fwd_noalloc(p, 4096, 4096, w.cutoff)
