@@ -83,6 +83,25 @@ __device__ __forceinline__ float2 transfer_series(const BlasmDev& bl, const TFCo
   return make_float2(c * sc, s * sc);
 }
 
+// The same H_{c,l} (scale 1) where the caller knows the bin lies inside the band and there
+// is no aperture: phase polynomial and one sine/cosine, nothing else.
+__device__ __forceinline__ float2 transfer_inband(const TFConst& t, const TFCol& col, int sy) {
+  const float fy2 = (float)(sy * sy);
+  const float q = fmaf(t.qy, fy2, col.qx2);
+  const float num = fmaf(t.ay, fy2, col.ax2);
+  float g = fmaf(q, 0.01611328125f, 0.0205078125f);
+  g = fmaf(q, g, 0.02734375f);
+  g = fmaf(q, g, 0.0390625f);
+  g = fmaf(q, g, 0.0625f);
+  g = fmaf(q, g, 0.125f);
+  g = fmaf(q, g, 0.5f);
+  float turns = fmaf(-num, g, t.turns0);
+  turns -= rintf(turns);
+  float s, c;
+  __sincosf(6.28318530717958647692f * turns, &s, &c);
+  return make_float2(c, s);
+}
+
 __device__ __forceinline__ float2 transfer(const BlasmDev& bl, int cl, int sx, int sy,
                                            float scale) {
   const TFConst& t = bl.tf[cl];

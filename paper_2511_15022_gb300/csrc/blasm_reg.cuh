@@ -133,13 +133,31 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
 }
 
 // Column kernels work on float4 elements: columns 2 s and 2 s + 1 of the CTA's column block
-// transformed in lockstep (NB float4 slots, CB = 2 NB columns per CTA).
+// transformed in lockstep (NB float4 slots, CB = 2 NB columns per CTA).  The 1 / (Ny Nx)
+// of the inverse transform is applied once per element outside (to the parked spectrum in
+// the forward kernel, to the plane sum in the backward one), so H is taken with scale 1;
+// `inband` (both columns inside the band, every row inside it, no aperture: uniform across
+// a CTA of one column pair) drops the mask.
+template <bool CONJ>
 __device__ __forceinline__ float4 transfer_pair(const BlasmDev& bl, const TFConst& t,
                                                 const TFCol& c0, const TFCol& c1, int sy,
-                                                float4 v, bool conj_h) {
-  const float2 h0 = transfer_series(bl, t, c0, sy, bl.inv_ntot);
-  const float2 h1 = transfer_series(bl, t, c1, sy, bl.inv_ntot);
-  return conj_h ? pack(cmulc(lo(v), h0), cmulc(hi(v), h1)) : pack(cmul(lo(v), h0), cmul(hi(v), h1));
+                                                float4 v, bool inband) {
+  float2 h0, h1;
+  if (inband) {
+    h0 = transfer_inband(t, c0, sy);
+    h1 = transfer_inband(t, c1, sy);
+  } else {
+    h0 = transfer_series(bl, t, c0, sy, 1.0f);
+    h1 = transfer_series(bl, t, c1, sy, 1.0f);
+  }
+  return CONJ ? pack(cmulc(lo(v), h0), cmulc(hi(v), h1)) : pack(cmul(lo(v), h0), cmul(hi(v), h1));
+}
+
+// every row of the transform inside the band and no aperture (then only the column's own
+// band membership remains to check)
+template <int N>
+__device__ __forceinline__ bool rows_inband(const BlasmDev& bl, const TFConst& t) {
+  return bl.aperture2 <= 0.f && t.ky_max >= N / 2;
 }
 
 template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
@@ -170,7 +188,8 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
 #pragma unroll
     for (int i = 0; i < F::GC::MB; ++i)
 #pragma unroll
-      for (int r = 0; r < F::C; ++r) spec[(i * F::C + r) * T + threadIdx.x] = S[i][r];
+      for (int r = 0; r < F::C; ++r)
+        spec[(i * F::C + r) * T + threadIdx.x] = cscale(S[i][r], bl.inv_ntot);
   }
   for (int l = 0; l < bl.L; ++l) {
     const TFConst& tc = bl.tf[c * bl.L + l];
@@ -182,10 +201,11 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
         const int b = q % NB, j = q / NB;
         const TFCol c0 = tf_col(tc, signed_index(kb * CB + 2 * b, Nx));
         const TFCol c1 = tf_col(tc, signed_index(kb * CB + 2 * b + 1, Nx));
+        const bool inband = rows_inband<N>(bl, tc) && c0.in_band && c1.in_band;
 #pragma unroll
         for (int r = 0; r < I::A; ++r)
-          Z[i][r] = transfer_pair(bl, tc, c0, c1, signed_index(j + r * I::GA::M, N),
-                                  spec[(i * I::A + r) * T + threadIdx.x], false);
+          Z[i][r] = transfer_pair<false>(bl, tc, c0, c1, signed_index(j + r * I::GA::M, N),
+                                         spec[(i * I::A + r) * T + threadIdx.x], inband);
       }
     }
     reg::first_in_regs<N, I::A, NB, T, true>(Z);
@@ -232,9 +252,11 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
         const int b = q % NB, j = q / NB;
         const TFCol c0 = tf_col(tc, signed_index(kb * CB + 2 * b, Nx));
         const TFCol c1 = tf_col(tc, signed_index(kb * CB + 2 * b + 1, Nx));
+        const bool inband = rows_inband<N>(bl, tc) && c0.in_band && c1.in_band;
 #pragma unroll
         for (int r = 0; r < F::C; ++r) {
-          const float4 t = transfer_pair(bl, tc, c0, c1, signed_index(j + r * F::GC::M, N), S[i][r], true);
+          const float4 t = transfer_pair<true>(bl, tc, c0, c1, signed_index(j + r * F::GC::M, N),
+                                               S[i][r], inband);
           float4& a = accs[(i * F::C + r) * T + threadIdx.x];
           a = (l == 0) ? t : cadd(a, t);
         }
@@ -245,7 +267,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
 #pragma unroll
   for (int i = 0; i < I::GA::MB; ++i)
 #pragma unroll
-    for (int r = 0; r < I::A; ++r) acc[i][r] = accs[(i * I::A + r) * T + threadIdx.x];
+    for (int r = 0; r < I::A; ++r) acc[i][r] = cscale(accs[(i * I::A + r) * T + threadIdx.x], bl.inv_ntot);
   reg::first_in_regs<N, I::A, NB, T, true>(acc);
   float4 u[I::GC::MB][I::C];
   I::rest(acc, u, buf4, tw);
@@ -258,13 +280,17 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
 
 // ---------------------------------------------------------------- host launchers
 template <class K>
-inline cudaError_t reg_set_smem(K kernel, size_t bytes) {
+inline cudaError_t reg_set_smem(K kernel, size_t bytes, int resident) {
   cudaError_t e =
       cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
-  // the L1 / shared split is otherwise chosen per launch and can cap residency at one CTA
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared);
+  // ask for just the shared memory `resident` CTAs need (plus the 1 KB the system reserves
+  // per CTA): the split is otherwise chosen per launch and can cap residency at one CTA,
+  // while the maximum carve-out leaves L1 too small for the spill traffic
+  const size_t per_sm = 228u * 1024u;
+  size_t pct = (100u * (size_t)resident * (bytes + 1024u) + per_sm - 1) / per_sm;
+  if (pct > 100u) pct = 100u;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)pct);
 }
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
@@ -276,7 +302,7 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
   switch (kind) {
     case SPEC_ROWS_PAD_FWD: {
       auto k = kr_rows_pad_fwd<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, P::SMEM);
+      e = reg_set_smem(k, P::SMEM, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_PAD_FWD, s);
       k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->in, a->out);
@@ -285,7 +311,7 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
     }
     case SPEC_ROWS_INV_CROP: {
       auto k = kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, P::SMEM);
+      e = reg_set_smem(k, P::SMEM, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_INV_CROP, s);
       k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->in, a->out);
@@ -294,7 +320,7 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
     }
     default: {
       auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, P::SMEM);
+      e = reg_set_smem(k, P::SMEM, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_LOSS, s);
       k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad);
@@ -315,14 +341,14 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
   cudaError_t e = cudaSuccess;
   if (kind == SPEC_COLS_FWD_PLANES) {
     auto k = kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB>;
-    e = reg_set_smem(k, P::SMEM_SLOTS);
+    e = reg_set_smem(k, P::SMEM_SLOTS, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
     k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
     auto k = kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB>;
-    e = reg_set_smem(k, P::SMEM_SLOTS);
+    e = reg_set_smem(k, P::SMEM_SLOTS, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
     k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);

@@ -19,9 +19,9 @@
 //     first pass (stride-R stores) is laid out in rows of R padded to an odd length, which
 //     makes those stores bank-conflict free; the other buffer is dense.  Batch slots are
 //     interleaved innermost ([position][b]).
-// Twiddles: one FP32 table lookup exp(-2 pi i k / (Ns R)) per butterfly (table built in FP64
-// on the host), higher powers by complex multiplication; shared-memory addresses of every
-// pass are base + r * stride.
+// Twiddles: exp(-2 pi i k / (Ns R)) from one hardware sine/cosine per butterfly, higher
+// powers by complex multiplication; shared-memory addresses of every pass are
+// base + r * stride.
 #pragma once
 
 #include "fft.cuh"
@@ -64,12 +64,13 @@ struct BufSize {
 template <int N, int R, int NS, bool INV, class E>
 __device__ __forceinline__ void twiddle(E (&v)[R], int j, const float2* __restrict__ tw) {
   if constexpr (NS > 1) {
-    // one lookup of exp(-2 pi i k / (NS R)); its powers by complex multiplication (a
-    // lookup per power was slower: load latency at this occupancy outweighs 4 FMAs)
+    // w = exp(-+2 pi i k / (NS R)) from the hardware sine/cosine (the angle lies in
+    // [0, 2 pi / R), inside the range where it is accurate to ~4e-7), its powers by complex
+    // multiplication; no memory access, so no load latency to hide at this occupancy
     const int k = j % NS;
-    constexpr int stride = N / (NS * R);
-    float2 w = __ldg(tw + k * stride);
-    if (INV) w.y = -w.y;
+    float s, c;
+    __sincosf((float)k * (float)(6.28318530717958647692 / (NS * R)), &s, &c);
+    float2 w = make_float2(c, INV ? s : -s);
     float2 p = w;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
