@@ -34,7 +34,8 @@ from paper_2511_15022_gb300.optim import LRS  # noqa: E402  (Adam rates per grou
 
 def algorithmic_bytes(w) -> dict:
     """Compulsory HBM bytes per launch of each FFT-pass kernel: complex64 units of
-    S = H*W*8 bytes per channel (pad / crop halves skipped, planes fused)."""
+    S = H*W*8 bytes per channel (pad / crop halves skipped, planes fused).  rows_loss is the
+    fused pass with the gradient; the forward-only launch moves 2.5 units instead of 4.5."""
     S = w.H * w.W * 8
     C, L = w.C, w.L
     return {
@@ -46,6 +47,79 @@ def algorithmic_bytes(w) -> dict:
         "k_raster_fwd": 1 * C * S,
         "k_raster_bwd": 1 * C * S,
     }
+
+
+def raster_pairs(p: dict, cutoff: float) -> float:
+    """Estimated number of (pixel, Gaussian) pairs with alpha * G >= cutoff: the area of each
+    Gaussian's cutoff ellipse, 2 pi ln(alpha / t) sqrt(det Sigma) (image borders ignored)."""
+    import numpy as np
+    s = np.exp(p["s_raw"].astype(np.float64)) + 0.1
+    th = p["theta"].astype(np.float64)
+    a = 1.0 / (1.0 + np.exp(-p["alpha_raw"].astype(np.float64)))
+    c, si = np.cos(th), np.sin(th)
+    s0, s1 = s[:, 0] ** 2, s[:, 1] ** 2
+    S00 = c * c * s0 + si * si * s1 + 0.1
+    S11 = si * si * s0 + c * c * s1 + 0.1
+    S01 = c * si * (s0 - s1)
+    det = S00 * S11 - S01 * S01
+    m = np.where(a > cutoff, 2.0 * np.log(np.minimum(a, 0.99) / cutoff), 0.0)
+    return float(np.sum(np.pi * m * np.sqrt(np.maximum(det, 0.0))))
+
+
+def step_work(w, mode: str, pairs: float) -> dict:
+    """Algorithmic work of one optimisation step per kernel: HBM bytes, FP32 flops (FFT
+    5 n log2 n per length-n transform plus 6 per transfer-function multiply; raster 15 per
+    pair forward, 45 backward) and MUFU operations (2 per transfer-function bin and plane,
+    1 exponential per raster pair).  mode 'autograd' runs a forward-only pass (raster, rows,
+    columns, loss rows without gradient) before the fused step."""
+    import math
+    H, W, C, L = w.H, w.W, w.C, w.L
+    Ny, Nx = w.pad * H, w.pad * W
+    S = H * W * 8
+    fx = 5.0 * Nx * math.log2(Nx)   # one row transform
+    fy = 5.0 * Ny * math.log2(Ny)   # one column transform
+    bins = C * L * Ny * Nx
+    fwd_pass = 2 if mode == "autograd" else 1
+    N = w.N
+    work = {
+        "k_rows_pad_fwd": (3 * C * S, C * H * fx, 0.0, fwd_pass),
+        "k_cols_fwd_planes": ((2 + 2 * L) * C * S, C * Nx * (1 + L) * fy + 6.0 * bins, 2.0 * bins,
+                              fwd_pass),
+        "k_cols_bwd_planes": ((2 * L + 2) * C * S, C * Nx * (L + 1) * fy + 6.0 * bins, 2.0 * bins, 1),
+        "k_rows_inv_crop": (3 * C * S, C * H * fx, 0.0, 1),
+        "k_raster_fwd": (C * S + 48.0 * N, 15.0 * pairs, pairs, fwd_pass),
+        "k_raster_bwd": (C * S + 96.0 * N, 45.0 * pairs, pairs, 1),
+        "k_adam": (7 * 4.0 * (6 + 2 * C) * N, 0.0, 0.0, 1),
+    }
+    # amounts per step: kernels of the forward-only pass run twice in autograd mode
+    work = {k: (b * n, f * n, u * n, n) for k, (b, f, u, n) in work.items()}
+    grad_rows = (4.5 * L * C * S, L * C * H * 2 * fx, 0.0)
+    if mode == "autograd":  # one forward-only launch + one with the gradient
+        nograd = (2.5 * L * C * S, L * C * H * fx, 0.0)
+        work["k_rows_loss"] = tuple(a + b for a, b in zip(nograd, grad_rows)) + (2,)
+    else:
+        work["k_rows_loss"] = grad_rows + (1,)
+    return work
+
+
+def rooflines(work: dict, prof: dict, steps: int, hbm_gbs: float, fp32_peak: float,
+              sfu_peak: float) -> dict:
+    """Per kernel and per step: time bound = max(bytes / HBM, flops / FP32, MUFU ops / SFU)
+    against the measured per-step time of the kernel (FP32 peak from the unit counts and
+    clock, MUFU peak from the microbenchmark)."""
+    rows, floor_total = {}, 0.0
+    for k, (b, f, u, launches) in work.items():
+        t = {"hbm": b / (hbm_gbs * 1e9), "fp32": f / fp32_peak, "sfu": u / sfu_peak}
+        bound = max(t, key=t.get)
+        floor_total += t[bound]
+        meas = prof[k]["ms"] / steps / 1e3 if k in prof else None
+        rows[k] = {"bound": bound, "floor_us": round(t[bound] * 1e6, 1),
+                   "hbm_us": round(t["hbm"] * 1e6, 1), "fp32_us": round(t["fp32"] * 1e6, 1),
+                   "sfu_us": round(t["sfu"] * 1e6, 1),
+                   "measured_us": round(meas * 1e6, 1) if meas else None,
+                   "frac": round(t[bound] / meas, 3) if meas else None,
+                   "launches_per_step": launches}
+    return {"per_kernel_per_step": rows, "step_floor_ms": floor_total * 1e3}
 
 
 class ClockSampler:
@@ -222,9 +296,81 @@ def torch_blasm_ms(w, dev, steps: int = 10) -> dict:
         once()
     e1.record()
     torch.cuda.synchronize()
-    return {"ms_per_step": e0.elapsed_time(e1) / steps,
-            "peak_mem_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
-            "what": "PyTorch autograd + cuFFT BLASM fwd+bwd incl. intensity MSE (no raster)"}
+    autograd_ms = e0.elapsed_time(e1) / steps
+    peak_gb = torch.cuda.max_memory_allocated(dev) / 1e9
+
+    # cuFFT alone: the 2-D transforms a BLASM forward + adjoint needs on the padded grid
+    # (1 forward + L inverse, then L forward + 1 inverse), nothing else
+    P = torch.randn(C, Ny, Nx, dtype=torch.complex64, device=dev)
+    Q = torch.randn(L, C, Ny, Nx, dtype=torch.complex64, device=dev)
+
+    def ffts():
+        torch.fft.fft2(P)
+        torch.fft.ifft2(Q)
+        torch.fft.fft2(Q)
+        torch.fft.ifft2(P)
+
+    for _ in range(3):
+        ffts()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        ffts()
+    e1.record()
+    torch.cuda.synchronize()
+    return {"ms_per_step": autograd_ms, "peak_mem_gb": peak_gb,
+            "what": "PyTorch autograd + cuFFT BLASM fwd+bwd incl. intensity MSE (no raster)",
+            "cufft_only_ms": e0.elapsed_time(e1) / steps,
+            "cufft_only_what": (f"cuFFT 2-D transforms of the padded {Ny}x{Nx} grid: "
+                                f"{2 * (1 + L)} x {C} channels (no pad, H, crop or loss)")}
+
+
+# ------------------------------------------------------------------ 4K stress
+def stress_4k(dev, steps: int = 5, warmup: int = 2) -> dict:
+    """2160 x 3840 RGB hologram, 1M Gaussians (scales 0.3-8 px), 6 planes z ~ U[0, 20] mm:
+    fused step + Adam.  Reports iterations/s and the allocator's peak device memory for the
+    parameters, Adam state, target, gradients and the plan's workspace."""
+    import torch
+
+    from paper_2511_15022_gb300 import cgh, inputs
+    w = inputs.uhd_4k()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    base = torch.cuda.memory_allocated(dev)
+    torch.cuda.reset_peak_memory_stats(dev)
+    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
+                    max_gaussians=w.N, device=dev)
+    p = {k: torch.from_numpy(v).to(dev) for k, v in inputs.params_for(w).items()}
+    gen = torch.Generator(device=dev).manual_seed(inputs.SEED_TARGETS)
+    target = torch.rand((w.L, w.C, w.H, w.W), generator=gen, device=dev)
+    g = plan.empty_grads(w.N)
+    m = {k: torch.zeros_like(v) for k, v in p.items()}
+    v2 = {k: torch.zeros_like(v) for k, v in p.items()}
+    loss = torch.empty(1, device=dev)
+    it = [0]
+
+    def one():
+        plan.step(p, target, grads=g, loss_out=loss)
+        it[0] += 1
+        cgh.adam_step([(p[k], g[k], m[k], v2[k], LRS[k]) for k in cgh.PARAM_KEYS], it[0])
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": w.name, "z_mm": [round(z * 1e3, 3) for z in w.z_m],
+           "it_per_s": 1000.0 / ms, "ms_per_step": ms,
+           "peak_device_mem_gb": (torch.cuda.max_memory_allocated(dev) - base) / 1e9,
+           "workspace_gb": plan.workspace_bytes / 1e9, "steps": steps,
+           "what": "fused step (cgh_step) + Adam, target uniform random"}
+    plan.close()
+    return out
 
 
 # ------------------------------------------------------------------ batched holograms
@@ -457,8 +603,7 @@ def main():
                     help="run the learned-initialiser extra on all 2000 targets")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-holograms and time-to-PSNR measurements")
-    ap.add_argument("--torch-baseline", action="store_true",
-                    help="also time the PyTorch-autograd + cuFFT propagation stage (context)")
+
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -593,23 +738,46 @@ def main():
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
-        alg = algorithmic_bytes(w)
-        fft_kernels = {k: v for k, v in prof.items() if k in alg and k.startswith("k_")}
-        dominant = max(prof.items(), key=lambda kv: kv[1]["ms"])[0] if prof else None
+        alu = cgh.measure_peaks()
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        # FP32 peak from the unit counts and the sampled clock: SMs x 128 FP32 lanes x 2 flops
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_nominal = sms * 128 * 2 * sm_mhz * 1e6
+        work = step_work(w, args.mode, raster_pairs(params_np, w.cutoff))
+        roof = rooflines(work, prof, args.steps, peak, fp32_nominal, alu["sfu_ops_per_s"])
         per_kernel = {k: {"ms_per_launch": v["ms"] / v["launches"], "launches": v["launches"],
                           "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
                       for k, v in prof.items()}
-        roof_k = dominant if dominant in alg else max(fft_kernels, key=lambda k: prof[k]["ms"])
+        # the dominant kernel (most device time per step) and its own bound
+        roof_k = max((k for k in prof if k in work), key=lambda k: prof[k]["ms"])
+        b, f, u, n_launch = work[roof_k]
         avg_s = prof[roof_k]["ms"] / prof[roof_k]["launches"] / 1000.0
-        achieved = alg[roof_k] / avg_s / 1e9
+        bound = roof["per_kernel_per_step"][roof_k]["bound"]
         traffic = profiled_traffic(roof_k)
-        roofline = {"kernel": roof_k, "bound": "hbm", "achieved": achieved, "peak": peak,
-                    "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+        if bound == "hbm":
+            achieved, pk, unit = b / n_launch / avg_s / 1e9, peak, "GB/s"
+            peak_source = f"{peak_kind} HBM copy bandwidth"
+        else:
+            achieved, pk, unit = f / n_launch / avg_s / 1e12, fp32_nominal / 1e12, "TFLOP/s"
+            peak_source = (f"FP32: {sms} SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (sampled); "
+                           f"microbenchmark measured {alu['fp32_flops_per_s'] / 1e12:.1f}")
+            bound = "alu"
+        roofline = {"kernel": roof_k, "bound": bound, "achieved": achieved, "peak": pk,
+                    "unit": unit, "frac": achieved / pk, "traffic": traffic,
                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                        "profiles/ (sources sha " + kernel_source_sha() + ")")
                     if traffic is not None else "no ncu capture of the current kernel sources",
-                    "peak_source": f"{peak_kind} HBM copy bandwidth",
-                    "algorithmic_bytes_per_launch": alg[roof_k]}
+                    "peak_source": peak_source,
+                    "algorithmic_bytes_per_launch": b / n_launch,
+                    "algorithmic_flops_per_launch": f / n_launch,
+                    "hbm_frac": (b / n_launch / avg_s / 1e9) / peak,
+                    "step": {"floor_ms": roof["step_floor_ms"],
+                             "frac": roof["step_floor_ms"] / (ms_total / args.steps),
+                             "what": "sum over kernels of max(HBM, FP32, MUFU) time floors"},
+                    "peaks": {"hbm_gbs": peak, "fp32_tflops_nominal": fp32_nominal / 1e12,
+                              "fp32_tflops_measured": alu["fp32_flops_per_s"] / 1e12,
+                              "sfu_tops_measured": alu["sfu_ops_per_s"] / 1e12},
+                    "per_kernel": roof["per_kernel_per_step"]}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             import oracle
@@ -629,13 +797,14 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "kernels": per_kernel, "clocks": clk,
-            "torch_cufft_blasm": torch_blasm_ms(w, dev) if args.torch_baseline else None,
+            "torch_cufft_blasm": torch_blasm_ms(w, dev) if not args.no_extras else None,
             "autotuned": tuned is not None,
         }
         if not args.no_extras and world == 1:
             line["batched"] = batched_bench(dev, steps=max(5, args.steps // 4), warmup=3)
             line["time_to_psnr"] = time_to_psnr(dev, plan_tuning=tuned)
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
+            line["stress_4k"] = stress_4k(dev)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

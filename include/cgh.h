@@ -294,6 +294,12 @@ cgh_status cgh_encoder_decode_bwd(int32_t B, int32_t CY, int32_t CX, int32_t S, 
                                   int32_t H, int32_t W, const cgh_grads* param_grads,
                                   float* dout, void* stream);
 
+/* Measurement utility (no counterpart in the paper): FP32 FMA throughput (flop/s, one FMA
+ * = 2 flops) and MUFU throughput (special-function operations/s) of the current device,
+ * from two microbenchmark kernels timed with CUDA events on `stream` (synchronous, ~50 ms).
+ * These are the denominators of the arithmetic rooflines the benchmark reports. */
+cgh_status cgh_measure_peaks(double* fp32_flops_per_s, double* sfu_ops_per_s, void* stream);
+
 /* Number of kernels launched by this thread's calls into the library so far (host
  * counter; used to report launches per step). */
 int64_t cgh_launch_count(void);

@@ -52,7 +52,7 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
            "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
            "cgh_autotune", "cgh_conv3x3_fwd", "cgh_conv3x3_bwd", "cgh_cast_bf16",
-           "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad")
+           "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad", "cgh_measure_peaks")
 
 
 def library_path() -> str:
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_encoder_decode_bwd.argtypes = [i32, i32, i32, i32, i32, i32, i32,
                                            ctypes.POINTER(_Grads), vp, vp]
     lib.cgh_mse_grad.argtypes = [i64, vp, vp, f32, i32, vp, vp, vp]
+    lib.cgh_measure_peaks.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(f64), vp]
     lib.cgh_launch_count.restype = i64
     lib.cgh_last_error_string.restype = ctypes.c_char_p
     lib.cgh_profile_enable.argtypes = [i32]
@@ -144,6 +145,15 @@ def _need(t: torch.Tensor, dtype: torch.dtype, shape, name: str):
         raise CGHError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
     if not t.is_contiguous():
         raise CGHError(f"{name} must be contiguous")
+
+
+def measure_peaks(stream=None) -> Dict[str, float]:
+    """cgh_measure_peaks: FP32 flop/s and MUFU op/s of the current device."""
+    lib = load()
+    f, u = ctypes.c_double(), ctypes.c_double()
+    _check(lib.cgh_measure_peaks(ctypes.byref(f), ctypes.byref(u), ctypes.c_void_p(_stream(stream))),
+           "cgh_measure_peaks")
+    return {"fp32_flops_per_s": f.value, "sfu_ops_per_s": u.value}
 
 
 def launch_count() -> int:

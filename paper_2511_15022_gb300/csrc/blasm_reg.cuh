@@ -84,12 +84,29 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
   });
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// tstage = 1: the CTA's NB target rows are copied into shared memory (after the exchange
+// buffer) with asynchronous 16-byte copies issued before the inverse transform, so their
+// latency hides behind it (needs a 16-byte aligned target and W % 4 == 0).
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_constant__ BlasmDev bl,
                                                   const float2* __restrict__ tw,
                                                   float2* __restrict__ V,
                                                   const float* __restrict__ target,
-                                                  float* __restrict__ partials, int want_grad) {
+                                                  float* __restrict__ partials, int want_grad,
+                                                  int tstage) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using F = typename P::F;
   using I = typename P::I;
@@ -99,6 +116,16 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   const int batch = blockIdx.y, y0 = blockIdx.x * NB;  // batch = l * C + c
   const int H = bl.H, W = bl.W, ox = bl.ox;
   float2* half = V + (size_t)batch * H * N;
+  const float* tg = target + (size_t)batch * H * W;
+  float* tsm = reinterpret_cast<float*>(buf + P::BUF);
+  if (tstage) {
+    const int chunks = NB * (W / 4);
+    for (int i = threadIdx.x; i < chunks; i += T) {
+      const int b = i / (W / 4), x = (i % (W / 4)) * 4;
+      if (y0 + b < H) cp_async16(&tsm[b * W + x], &tg[(size_t)(y0 + b) * W + x]);
+    }
+    cp_async_commit();
+  }
   float2 v[I::GA::MB][I::A];
   reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
     const int y = y0 + b;
@@ -106,14 +133,18 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   });
   float2 u[I::GC::MB][I::C];
   I::rest(v, u, buf, tw);
+  if (tstage) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
   const float gscale = 4.0f / ((float)bl.L * (float)bl.C * (float)H * (float)W);
-  const float* tg = target + (size_t)batch * H * W;
   float acc = 0.f;
   reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
     const int x = a - ox, y = y0 + b;
     if (x >= 0 && x < W && y < H) {
       const float I_ = fmaf(val.x, val.x, val.y * val.y);
-      const float d = I_ - __ldg(&tg[(size_t)y * W + x]);
+      const float t_ = tstage ? tsm[b * W + x] : __ldg(&tg[(size_t)y * W + x]);
+      const float d = I_ - t_;
       acc = fmaf(d, d, acc);
       val = cscale(val, gscale * d);
     } else {
@@ -320,10 +351,12 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
     }
     default: {
       auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, P::SMEM, CGH_REG_MINB(T));
+      const int tstage = (p->W % 4 == 0 && (reinterpret_cast<uintptr_t>(a->target) & 15u) == 0);
+      const size_t smem = P::SMEM + (tstage ? sizeof(float) * (size_t)NB * p->W : 0);
+      e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_LOSS, s);
-      k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad);
+      k<<<grid, T, smem, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad, tstage);
       prof_end(KID_ROWS_LOSS, s);
       break;
     }
