@@ -191,7 +191,9 @@ __device__ __forceinline__ bool rows_inband(const BlasmDev& bl, const TFConst& t
   return bl.aperture2 <= 0.f && t.ky_max >= N / 2;
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
+// INBAND: every bin of every channel and plane lies inside the band and there is no
+// aperture (checked on the host), so the masked evaluation of H is not even compiled.
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB, bool INBAND>
 __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_constant__ BlasmDev bl,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ Y,
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
         const int b = q % NB, j = q / NB;
         const TFCol c0 = tf_col(tc, signed_index(kb * CB + 2 * b, Nx));
         const TFCol c1 = tf_col(tc, signed_index(kb * CB + 2 * b + 1, Nx));
-        const bool inband = rows_inband<N>(bl, tc) && c0.in_band && c1.in_band;
+        const bool inband = INBAND || (rows_inband<N>(bl, tc) && c0.in_band && c1.in_band);
 #pragma unroll
         for (int r = 0; r < I::A; ++r)
           Z[i][r] = transfer_pair<false>(bl, tc, c0, c1, signed_index(j + r * I::GA::M, N),
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
   }
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB, bool INBAND>
 __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_constant__ BlasmDev bl,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ G,
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
         const int b = q % NB, j = q / NB;
         const TFCol c0 = tf_col(tc, signed_index(kb * CB + 2 * b, Nx));
         const TFCol c1 = tf_col(tc, signed_index(kb * CB + 2 * b + 1, Nx));
-        const bool inband = rows_inband<N>(bl, tc) && c0.in_band && c1.in_band;
+        const bool inband = INBAND || (rows_inband<N>(bl, tc) && c0.in_band && c1.in_band);
 #pragma unroll
         for (int r = 0; r < F::C; ++r) {
           const float4 t = transfer_pair<true>(bl, tc, c0, c1, signed_index(j + r * F::GC::M, N),
@@ -350,8 +352,8 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       break;
     }
     default: {
-      auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
       const int tstage = (p->W % 4 == 0 && (reinterpret_cast<uintptr_t>(a->target) & 15u) == 0);
+      auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
       const size_t smem = P::SMEM + (tstage ? sizeof(float) * (size_t)NB * p->W : 0);
       e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
@@ -372,15 +374,20 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
   dim3 grid(p->bl.Nx / (2 * NB), p->C);
   const float2* tw = p->fy.tw;
   cudaError_t e = cudaSuccess;
+  bool all_in = p->bl.aperture2 <= 0.f;
+  for (int i = 0; i < p->C * p->L; ++i)
+    all_in = all_in && p->bl.tf[i].kx_max >= p->bl.Nx / 2 && p->bl.tf[i].ky_max >= N / 2;
   if (kind == SPEC_COLS_FWD_PLANES) {
-    auto k = kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB>;
+    auto k = all_in ? kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, true>
+                    : kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
     e = reg_set_smem(k, P::SMEM_SLOTS, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
     k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
-    auto k = kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB>;
+    auto k = all_in ? kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, true>
+                    : kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
     e = reg_set_smem(k, P::SMEM_SLOTS, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
