@@ -14,9 +14,10 @@
 //   4. k_raster_fwd   one CTA per tile, one thread per pixel; the tile's Gaussians are
 //                     staged in shared memory 256 at a time; each warp owns an 8x4 pixel
 //                     block and skips (warp-uniformly) Gaussians whose box misses it.
-//   5. k_raster_bwd   same traversal; per-pair gradient terms are reduced across the warp
-//                     with shuffles, accumulated per staged Gaussian with shared-memory
-//                     atomics, and flushed once per tile with global atomics.
+//   5. k_raster_bwd   one CTA per tile with the tile's dL/dU in shared memory; each warp
+//                     takes one Gaussian at a time and sweeps its box inside the tile,
+//                     accumulating the gradient moments in registers, then reduces them
+//                     across the warp with shuffles and adds them with global atomics.
 //   6. k_grad_finalize one thread per Gaussian: chain rule from the accumulated moments to
 //                     the pre-activation parameters (Suppl. items 1-7; the
 //                     inverse-covariance -> covariance step is the exact derivative of the
@@ -297,6 +298,12 @@ struct ReduceScatter<1, OFF> {
 //   [0, C)      P_c = sum a dL/dRe_c          [C, 2C)  Q_c = sum a dL/dIm_c
 //   2C          SG  = sum G S (unclamped pairs), S = sum_c (A_c dRe_c + B_c dIm_c)
 //   2C+1..2C+5  sum u dx, u dy, u dx^2, u dx dy, u dy^2 with u = S alpha G (power unclamped)
+// One CTA per tile.  The tile's dL/dU is staged in shared memory; each warp takes one staged
+// Gaussian at a time and sweeps the pixels of its box inside the tile (8 x 4 or 16 x 2
+// lanes per step, by the box width), accumulating the moments in registers; one
+// reduce-scatter over the warp and NV global atomics per (Gaussian, tile) follow.  Pixels
+// outside the box fail the cutoff test anyway (the box bounds the cutoff ellipse with
+// margin), so the sum equals that over all pixels of the tile.
 template <int C>
 __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float4* __restrict__ rec,
                                                     const int4* __restrict__ rect,
@@ -307,84 +314,85 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
   constexpr int NV = 2 * C + 6;
   constexpr int NVP = NV <= 8 ? 8 : 16;  // padded to a power of two for the reduce-scatter
   __shared__ float4 srec[256 * CGH_REC_F4];
-  __shared__ float sacc[256 * NV];
   __shared__ int sgid[256];
+  __shared__ float2 sdu[C][CGH_TILE * CGH_TILE];
   const int tx = blockIdx.x, ty = blockIdx.y;
   const int tile = ty * rc.tiles_x + tx;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wx0 = tx * CGH_TILE + (warp & 1) * 8, wy0 = ty * CGH_TILE + (warp >> 1) * 4;
-  const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
-  const float fpx = (float)px, fpy = (float)py;
-  const float fwx0 = (float)wx0, fwx1 = (float)(wx0 + 7), fwy0 = (float)wy0,
-              fwy1 = (float)(wy0 + 3);
-  const bool inside = px < rc.W && py < rc.H;
-  float gR[C], gI[C];
+  const int ox = tx * CGH_TILE, oy = ty * CGH_TILE;
   {
+    const int px = ox + (threadIdx.x & (CGH_TILE - 1)), py = oy + (threadIdx.x >> 4);
+    const bool inside = px < rc.W && py < rc.H;
     const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      float2 g = inside ? dU[c * plane + o] : make_float2(0.f, 0.f);
-      gR[c] = g.x;
-      gI[c] = g.y;
-    }
+    for (int c = 0; c < C; ++c) sdu[c][threadIdx.x] = inside ? dU[c * plane + o] : make_float2(0.f, 0.f);
   }
   const int start = tile_start[tile], end = tile_start[tile + 1];
   const bool exhaustive = (long long)end > rc.cap;
   const int count = exhaustive ? rc.N : end - start;
+  const float fox = (float)ox, foy = (float)oy;
   for (int base = 0; base < count; base += 256) {
     __syncthreads();
     const int nb = stage_batch(rc, rec, rect, pairs, start, count, exhaustive, base, tx, ty,
                                srec, sgid);
-    for (int t = threadIdx.x; t < 256 * NV; t += 256) sacc[t] = 0.f;
     __syncthreads();
-    for (int j = 0; j < nb; ++j) {
+    for (int j = warp; j < nb; j += 8) {
       const float4 bb = srec[j * CGH_REC_F4 + 2];
-      if (bb.y < fwx0 || bb.x > fwx1 || bb.w < fwy0 || bb.z > fwy1) continue;  // warp-uniform
+      // pixel box of the Gaussian inside this tile (tile coordinates)
+      const int x0 = (int)ceilf(fmaxf(bb.x, fox)) - ox;
+      const int x1 = (int)floorf(fminf(bb.y, fox + (float)(CGH_TILE - 1))) - ox;
+      const int y0 = (int)ceilf(fmaxf(bb.z, foy)) - oy;
+      const int y1 = (int)floorf(fminf(bb.w, foy + (float)(CGH_TILE - 1))) - oy;
+      if (x0 > x1 || y0 > y1) continue;  // warp-uniform
       const float4 r0 = srec[j * CGH_REC_F4 + 0];
       const float4 r1 = srec[j * CGH_REC_F4 + 1];
-      const float dx = fpx - r0.x, dy = fpy - r0.y;
-      const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
-      const bool pass = inside && p2 >= r1.y;
-      if (!__any_sync(0xffffffffu, pass)) continue;
-      float val[NVP];
+      const float4 r3 = srec[j * CGH_REC_F4 + 3];
+      const float4 r4 = srec[j * CGH_REC_F4 + 4];
+      const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+      const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+      const int lsh = (x1 - x0 >= 8) ? 4 : 3;  // lanes per row: 16 or 8
+      const int lx = lane & ((1 << lsh) - 1), ly = lane >> lsh, lrows = 32 >> lsh;
+      float acc[NVP];
 #pragma unroll
-      for (int v = 0; v < NVP; ++v) val[v] = 0.f;
-      if (pass) {
-        const float4 r3 = srec[j * CGH_REC_F4 + 3];
-        const float4 r4 = srec[j * CGH_REC_F4 + 4];
-        const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
-        const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
-        const float G = exp2f(fmaxf(p2, kP2Floor));
-        const float aG = r1.z * G;
-        const float a = fminf(kAlphaCap, aG);
-        float S = 0.f;
+      for (int v = 0; v < NVP; ++v) acc[v] = 0.f;
+      for (int by = y0; by <= y1; by += lrows) {
+        const int ly_ = by + ly;
+        for (int bx = x0; bx <= x1; bx += (1 << lsh)) {
+          const int lx_ = bx + lx;
+          if (lx_ > x1 || ly_ > y1) continue;
+          const float dx = (float)(ox + lx_) - r0.x, dy = (float)(oy + ly_) - r0.y;
+          const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
+          if (p2 < r1.y) continue;
+          const int pix = ly_ * CGH_TILE + lx_;
+          const float G = exp2f(fmaxf(p2, kP2Floor));
+          const float aG = r1.z * G;
+          const float a = fminf(kAlphaCap, aG);
+          float S = 0.f;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          val[c] = a * gR[c];
-          val[C + c] = a * gI[c];
-          S = fmaf(Ac[c], gR[c], fmaf(Bc[c], gI[c], S));
-        }
-        if (aG < kAlphaCap) {
-          val[2 * C] = S * G;
-          if (p2 > kP2Floor) {
-            const float u = S * aG;
-            const float udx = u * dx, udy = u * dy;
-            val[2 * C + 1] = udx;
-            val[2 * C + 2] = udy;
-            val[2 * C + 3] = udx * dx;
-            val[2 * C + 4] = udx * dy;
-            val[2 * C + 5] = udy * dy;
+          for (int c = 0; c < C; ++c) {
+            const float2 g = sdu[c][pix];
+            acc[c] = fmaf(a, g.x, acc[c]);
+            acc[C + c] = fmaf(a, g.y, acc[C + c]);
+            S = fmaf(Ac[c], g.x, fmaf(Bc[c], g.y, S));
+          }
+          if (aG < kAlphaCap) {
+            acc[2 * C] = fmaf(S, G, acc[2 * C]);
+            if (p2 > kP2Floor) {
+              const float u = S * aG;
+              const float udx = u * dx, udy = u * dy;
+              acc[2 * C + 1] += udx;
+              acc[2 * C + 2] += udy;
+              acc[2 * C + 3] = fmaf(udx, dx, acc[2 * C + 3]);
+              acc[2 * C + 4] = fmaf(udx, dy, acc[2 * C + 4]);
+              acc[2 * C + 5] = fmaf(udy, dy, acc[2 * C + 5]);
+            }
           }
         }
       }
       int vidx = 0;
-      ReduceScatter<NVP, 16>::run(val, lane, vidx);
-      if ((lane & (32 / NVP - 1)) == 0 && vidx < NV) atomicAdd(&sacc[j * NV + vidx], val[0]);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nb * NV; t += 256) {
-      const float v = sacc[t];
-      if (v != 0.f) atomicAdd(&raw[(size_t)sgid[t / NV] * CGH_RAW_STRIDE + (t % NV)], v);
+      ReduceScatter<NVP, 16>::run(acc, lane, vidx);
+      if ((lane & (32 / NVP - 1)) == 0 && vidx < NV && acc[0] != 0.f)
+        atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
     }
   }
 }
