@@ -13,7 +13,8 @@
 //                     sort of (tile, depth) keys.
 //   4. k_raster_fwd   one CTA per tile, one thread per pixel; the tile's Gaussians are
 //                     staged in shared memory 256 at a time; each warp owns an 8x4 pixel
-//                     block and skips (warp-uniformly) Gaussians whose box misses it.
+//                     block and visits only the staged Gaussians whose box touches it
+//                     (per-warp lists compacted with ballots).
 //   5. k_raster_bwd   one CTA per tile with the tile's dL/dU in shared memory; each warp
 //                     takes one Gaussian at a time and sweeps its box inside the tile,
 //                     accumulating the gradient moments in registers, then reduces them
@@ -211,6 +212,10 @@ __device__ __forceinline__ int stage_batch(const RasterConsts& rc, const float4*
   return min(256, count - base);
 }
 
+// Forward: one CTA per tile, one thread per pixel; warp w owns the 8 x 4 block at
+// ((w & 1) 8, (w >> 1) 4) of the tile.  When a batch is staged, the thread that staged a
+// Gaussian also marks which warp blocks its box touches; each warp then compacts its own
+// list with ballots and visits only those Gaussians.
 template <int C>
 __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float4* __restrict__ rec,
                                                     const int4* __restrict__ rect,
@@ -218,14 +223,15 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float
                                                     const int* __restrict__ pairs,
                                                     float2* __restrict__ U) {
   __shared__ float4 srec[256 * CGH_REC_F4];
+  __shared__ unsigned char smask[256];
+  __shared__ unsigned char slist[8][256];
   const int tx = blockIdx.x, ty = blockIdx.y;
   const int tile = ty * rc.tiles_x + tx;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wx0 = tx * CGH_TILE + (warp & 1) * 8, wy0 = ty * CGH_TILE + (warp >> 1) * 4;
   const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
   const float fpx = (float)px, fpy = (float)py;
-  const float fwx0 = (float)wx0, fwx1 = (float)(wx0 + 7), fwy0 = (float)wy0,
-              fwy1 = (float)(wy0 + 3);
+  const float fox = (float)(tx * CGH_TILE), foy = (float)(ty * CGH_TILE);
   const int start = tile_start[tile], end = tile_start[tile + 1];
   const bool exhaustive = (long long)end > rc.cap;
   const int count = exhaustive ? rc.N : end - start;
@@ -236,10 +242,29 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float
     __syncthreads();
     const int nb = stage_batch(rc, rec, rect, pairs, start, count, exhaustive, base, tx, ty,
                                srec, nullptr);
+    if (threadIdx.x < nb) {
+      // warp blocks (2 columns x 4 rows of the tile) the staged box touches
+      const float4 bb = srec[threadIdx.x * CGH_REC_F4 + 2];
+      unsigned m = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const float x0 = fox + (float)((w & 1) * 8), y0 = foy + (float)((w >> 1) * 4);
+        if (bb.y >= x0 && bb.x <= x0 + 7.f && bb.w >= y0 && bb.z <= y0 + 3.f) m |= 1u << w;
+      }
+      smask[threadIdx.x] = (unsigned char)m;
+    }
     __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-      const float4 bb = srec[j * CGH_REC_F4 + 2];
-      if (bb.y < fwx0 || bb.x > fwx1 || bb.w < fwy0 || bb.z > fwy1) continue;  // warp-uniform
+    int cnt = 0;
+    for (int k = 0; k < nb; k += 32) {
+      const int i = k + lane;
+      const bool mine = i < nb && ((smask[i] >> warp) & 1u);
+      const unsigned b = __ballot_sync(0xffffffffu, mine);
+      if (mine) slist[warp][cnt + __popc(b & ((1u << lane) - 1u))] = (unsigned char)i;
+      cnt += __popc(b);
+    }
+    __syncwarp();
+    for (int t = 0; t < cnt; ++t) {
+      const int j = slist[warp][t];
       const float4 r0 = srec[j * CGH_REC_F4 + 0];
       const float4 r1 = srec[j * CGH_REC_F4 + 1];
       const float dx = fpx - r0.x, dy = fpy - r0.y;
