@@ -217,13 +217,50 @@ struct SplitOf {
   static constexpr int B = R / A;
 };
 
-// Composite R = A * B: input n = B n1 + n2, output k = k1 + A k2.
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+// x with a x = 1 (mod m), for gcd(a, m) = 1 (m = 1: 0)
+constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return 0;
+}
+
+// Composite R = A * B.
+//   gcd(A, B) = 1: prime-factor (Good-Thomas) form, no twiddles: input n = (B n1 + A n2)
+//   mod R, output k = (eA k1 + eB k2) mod R with eA = 1 (mod A), 0 (mod B) and eB = 0
+//   (mod A), 1 (mod B); all indices are compile-time constants, so the maps are free.
+//   otherwise Cooley-Tukey: input n = B n1 + n2, output k = k1 + A k2, twiddles between.
 template <int R, bool INV>
 struct DFT {
   static_assert(R % SplitOf<R>::A == 0, "unsupported radix");
   template <class E>
   __device__ __forceinline__ static void run(E (&v)[R]) {
     constexpr int A = SplitOf<R>::A, B = SplitOf<R>::B;
+    if constexpr (gcd_c(A, B) == 1) {
+      constexpr int eA = B * inv_mod(B % A, A), eB = A * inv_mod(A % B, B);
+      E u[B][A];
+      sfor<0, B>([&](auto N2) {
+        constexpr int n2 = decltype(N2)::value;
+        E t[A];
+        sfor<0, A>([&](auto N1) {
+          constexpr int n1 = decltype(N1)::value;
+          t[n1] = v[(B * n1 + A * n2) % R];
+        });
+        DFT<A, INV>::run(t);
+        sfor<0, A>([&](auto K1) { u[n2][decltype(K1)::value] = t[decltype(K1)::value]; });
+      });
+      sfor<0, A>([&](auto K1) {
+        constexpr int k1 = decltype(K1)::value;
+        E t[B];
+        sfor<0, B>([&](auto N2) { t[decltype(N2)::value] = u[decltype(N2)::value][k1]; });
+        DFT<B, INV>::run(t);
+        sfor<0, B>([&](auto K2) {
+          constexpr int k2 = decltype(K2)::value;
+          v[(eA * k1 + eB * k2) % R] = t[k2];
+        });
+      });
+      return;
+    }
     E u[B][A];
     sfor<0, B>([&](auto N2) {
       constexpr int n2 = decltype(N2)::value;
