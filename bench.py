@@ -176,13 +176,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_sha() -> str:
-    """Hash of the CUDA sources: ncu traffic figures are valid only for the kernels they
-    were captured from."""
+FFT_SOURCES = ("fft.cuh", "fftreg.cuh", "blasm_common.cuh", "blasm_reg.cuh", "blasm_spec.h",
+               "blasm_spec_a.cu", "blasm_spec_b.cu", "blasm_spec_c.cu", "blasm.cu",
+               "cgh_internal.h")
+RASTER_SOURCES = ("raster.cu", "cgh_internal.h")
+
+
+def kernel_source_sha(kernel: str = "") -> str:
+    """Hash of the CUDA sources a kernel is built from (the FFT-pass files for k_rows_* /
+    k_cols_*, the rasteriser for k_raster_*, all of csrc otherwise): ncu traffic figures
+    are valid only for the kernel sources they were captured from."""
     import glob
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2511_15022_gb300", "csrc")
+    if kernel.startswith(("k_rows_", "k_cols_")):
+        files = [os.path.join(csrc, f) for f in FFT_SOURCES]
+    elif kernel.startswith("k_raster_"):
+        files = [os.path.join(csrc, f) for f in RASTER_SOURCES]
+    else:
+        files = glob.glob(os.path.join(csrc, "*"))
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2511_15022_gb300", "csrc", "*"))):
+    for f in sorted(files):
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
@@ -193,7 +207,7 @@ def profiled_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summaries (lines
     'traffic-per-launch <kernel> <bytes> sha=<sha>'), or None if absent or stale."""
     import glob
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     for f in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(f) as fh:
             for line in fh:
@@ -765,7 +779,7 @@ def main():
         roofline = {"kernel": roof_k, "bound": bound, "achieved": achieved, "peak": pk,
                     "unit": unit, "frac": achieved / pk, "traffic": traffic,
                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                       "profiles/ (sources sha " + kernel_source_sha() + ")")
+                                       "profiles/ (sources sha " + kernel_source_sha(roof_k) + ")")
                     if traffic is not None else "no ncu capture of the current kernel sources",
                     "peak_source": peak_source,
                     "algorithmic_bytes_per_launch": b / n_launch,
