@@ -18,7 +18,7 @@
 
 // resident CTAs per SM the register allocation is sized for
 #ifndef CGH_REG_MINB
-#define CGH_REG_MINB(T) ((T) <= 256 ? 3 : 2)
+#define CGH_REG_MINB(T) ((T) <= 256 ? 3 : (T) <= 512 ? 2 : 1)
 #endif
 
 namespace cgh {
