@@ -75,6 +75,8 @@ def _load():
         lib.orc_blasm_bwd.argtypes = [i, i, i, i, i, _dp, d, _dp, d, _dp, _dp]
         lib.orc_mse_loss.argtypes = [i, i, i, i, _dp, _dp, _dp]
         lib.orc_mse_loss.restype = d
+        lib.orc_recon_loss.argtypes = [i, i, i, i, _dp, _dp, ctypes.c_void_p, _dp]
+        lib.orc_recon_loss.restype = d
         lib.orc_psnr.argtypes = [i, i, i, i, _dp, _dp]
         lib.orc_psnr.restype = d
         lib.orc_adam.argtypes = [i64, _dp, _dp, _dp, _dp, d, d, d, d, i]
@@ -239,6 +241,24 @@ def mse_loss(Ud, target):
     return float(loss), dUd
 
 
+def recon_loss(Ud, target, mask=None):
+    """Three-term reconstruction loss L_recon (Sec. 3.2) with binary depth masks
+    mask [L, H, W] (None: M = 0).  Returns (loss, dL/dUd)."""
+    Ud = _c128(Ud)
+    L, C, H, W = Ud.shape
+    t = _f64(target)
+    assert t.shape == (L, C, H, W)
+    mptr = None
+    if mask is not None:
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        assert m.shape == (L, H, W)
+        mptr = m.ctypes.data_as(ctypes.c_void_p)
+    dUd = np.zeros_like(Ud)
+    loss = _load().orc_recon_loss(L, C, H, W, _ptr(Ud.view(np.float64)), _ptr(t), mptr,
+                                  _ptr(dUd.view(np.float64)))
+    return float(loss), dUd
+
+
 def psnr(Ud, target) -> float:
     Ud = _c128(Ud)
     L, C, H, W = Ud.shape
@@ -262,12 +282,17 @@ def forward(params: dict, H: int, W: int, lambdas, pitch: float, z, pad: int = 2
 
 
 def step(params: dict, target, H: int, W: int, lambdas, pitch: float, z, pad: int = 2,
-         cutoff: float = 1.0 / 255.0, aperture: float = 0.0, g_idx=None):
+         cutoff: float = 1.0 / 255.0, aperture: float = 0.0, g_idx=None, recon_mask=None,
+         loss: str = "mse"):
     """One forward + backward pass of the whole hot path (Algorithm 1 body without the
-    optimiser): raster -> pad -> multi-plane BLASM -> intensity MSE -> adjoint BLASM ->
+    optimiser): raster -> pad -> multi-plane BLASM -> intensity MSE (or, with
+    loss="recon", the three-term L_recon with depth masks recon_mask) -> adjoint BLASM ->
     raster backward.  Returns dict(loss, U0, Ud, dUd, dU0, grads)."""
     U0, Ud = forward(params, H, W, lambdas, pitch, z, pad, cutoff, aperture)
-    loss, dUd = mse_loss(Ud, target)
+    if loss == "recon":
+        loss, dUd = recon_loss(Ud, target, recon_mask)
+    else:
+        loss, dUd = mse_loss(Ud, target)
     dU0 = blasm_bwd(dUd, lambdas, pitch, z, pad, aperture)
     grads = raster_bwd(params, H, W, dU0, cutoff, g_idx)
     return {"loss": loss, "U0": U0, "Ud": Ud, "dUd": dUd, "dU0": dU0, "grads": grads}

@@ -491,6 +491,37 @@ double orc_mse_loss(int L, int C, int H, int W, const double* Ud, const double* 
     return acc * norm;
 }
 
+/* Reconstruction loss of Sec. 3.2 (the three-term L_recon):                             */
+/*   L = (1/L) sum_l mean_{c,p} [ (I - I^)^2 + (I M - I^ M)^2 + (I I^ - I^ I^)^2 ]         */
+/* with I = |Ud|^2, I^ the target and M_l the binary depth mask of plane l (one byte per    */
+/* pixel, shared by the colour channels; mask == NULL means M = 0).  The mean over c and p  */
+/* follows the same reading as orc_mse_loss.  Returns L; writes dL/dUd as (dRe, dIm).       */
+double orc_recon_loss(int L, int C, int H, int W, const double* Ud, const double* target,
+                      const unsigned char* mask, double* dUd) {
+    double norm = 1.0 / ((double)L * (double)C * (double)H * (double)W);
+    double acc = 0.0;
+    for (int l = 0; l < L; ++l)
+        for (int c = 0; c < C; ++c)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x) {
+                    size_t i = (((size_t)l * C + c) * H + y) * W + x;
+                    double M = mask ? (double)(mask[((size_t)l * H + y) * W + x] != 0) : 0.0;
+                    double re = Ud[2 * i], im = Ud[2 * i + 1];
+                    double I = re * re + im * im, T = target[i];
+                    double t1 = I - T;
+                    double t2 = I * M - T * M;
+                    double t3 = I * T - T * T;
+                    acc += t1 * t1 + t2 * t2 + t3 * t3;
+                    if (dUd) {
+                        /* dL/dI of the three squares */
+                        double dI = 2.0 * norm * (t1 + M * t2 + T * t3);
+                        dUd[2 * i] = dI * 2.0 * re;
+                        dUd[2 * i + 1] = dI * 2.0 * im;
+                    }
+                }
+    return acc * norm;
+}
+
 /* Plane-averaged PSNR of the reconstructed intensities against the targets (Sec. 5
  * reports PSNR averaged over planes); intensities are clipped to [0, 1]. */
 double orc_psnr(int L, int C, int H, int W, const double* Ud, const double* target) {
