@@ -339,6 +339,52 @@ def torch_blasm_ms(w, dev, steps: int = 10) -> dict:
                                 f"{2 * (1 + L)} x {C} channels (no pad, H, crop or loss)")}
 
 
+# ------------------------------------------------------------------ L_recon
+def recon_bench(dev, plan_tuning=None, steps: int = 20) -> dict:
+    """The paper's training loss L_recon (Sec. 3.2, three terms with binary depth masks from
+    a synthetic quantised depth map) fused into the loss row pass, against the plain
+    intensity MSE: fused step + Adam at 1080p, RGB, 3 planes, 200k Gaussians."""
+    import torch
+
+    from paper_2511_15022_gb300 import cgh, inputs
+    w = inputs.hd_1080p()
+    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
+                    max_gaussians=w.N, device=dev)
+    if plan_tuning:
+        plan.set_tuning(**{k: v for k, v in plan_tuning.items() if k != "pair_capacity_per_gaussian"})
+    p = {k: torch.from_numpy(v).to(dev) for k, v in inputs.params_for(w).items()}
+    t = torch.from_numpy(inputs.blob_targets(w.L, w.C, w.H, w.W)).to(dev)
+    mask = torch.from_numpy(inputs.depth_masks(w.L, w.H, w.W, seed=inputs.SEED_TARGETS)).to(dev)
+    g = plan.empty_grads(w.N)
+    m = {k: torch.zeros_like(v) for k, v in p.items()}
+    v2 = {k: torch.zeros_like(v) for k, v in p.items()}
+    loss = torch.empty(1, device=dev)
+    out = {}
+    for kind in ("mse", "recon"):
+        plan.set_loss(kind, mask if kind == "recon" else None)
+        it = [0]
+
+        def one():
+            plan.step(p, t, grads=g, loss_out=loss)
+            it[0] += 1
+            cgh.adam_step([(p[k], g[k], m[k], v2[k], LRS[k]) for k in cgh.PARAM_KEYS], it[0])
+
+        for _ in range(3):
+            one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            one()
+        e1.record()
+        torch.cuda.synchronize()
+        out[kind] = e0.elapsed_time(e1) / steps
+    plan.close()
+    return {"it_per_s_recon": 1000.0 / out["recon"], "it_per_s_mse": 1000.0 / out["mse"],
+            "ms_per_step_recon": out["recon"], "ms_per_step_mse": out["mse"],
+            "what": "fused step + Adam; L_recon weight 1 + M + T^2 applied in the loss row pass"}
+
+
 # ------------------------------------------------------------------ 4K stress
 def stress_4k(dev, steps: int = 5, warmup: int = 2) -> dict:
     """2160 x 3840 RGB hologram, 1M Gaussians (scales 0.3-8 px), 6 planes z ~ U[0, 20] mm:
@@ -827,6 +873,7 @@ def main():
             line["time_to_psnr"] = time_to_psnr(dev, plan_tuning=tuned)
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
             line["stress_4k"] = stress_4k(dev)
+            line["l_recon"] = recon_bench(dev, plan_tuning=tuned)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

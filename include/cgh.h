@@ -39,6 +39,8 @@
 extern "C" {
 #endif
 
+typedef enum { CGH_LOSS_MSE = 0, CGH_LOSS_RECON = 1 } cgh_loss_kind;
+
 typedef enum {
   CGH_OK = 0,
   CGH_ERR_ARG = 1,              /* invalid argument (null pointer, bad size, ...) */
@@ -125,6 +127,16 @@ cgh_status cgh_plan_get_tuning(const cgh_plan* plan, cgh_tuning* out);
  * largest |signed frequency index| that passes |f_x| < f_x^max (resp. y), index c*L + l.
  * Computed on the host in FP64 exactly as the definition reads. */
 cgh_status cgh_plan_band_limits(const cgh_plan* plan, int32_t* kx_max, int32_t* ky_max);
+
+/* Loss taken by cgh_intensity_loss, cgh_forward_loss, cgh_step and the batch step of this
+ * plan (Sec. 3.2).  kind = CGH_LOSS_MSE (default): L_MSE = 1/L sum_l mean_{c,p}
+ * (I_l - I^_l)^2.  kind = CGH_LOSS_RECON: the three-term reconstruction loss
+ *   L_recon = 1/L sum_l mean_{c,p} [ (I_l - I^_l)^2 + (I_l M_l - I^_l M_l)^2
+ *                                    + (I_l I^_l - I^_l I^_l)^2 ]
+ * with recon_mask the binary depth masks M_l: DEVICE bytes [L][H][W] (nonzero = 1, shared by
+ * the colour channels; NULL means M = 0), owned by the caller and read at every later call
+ * until the loss is set again.  A mask with CGH_LOSS_MSE is an argument error. */
+cgh_status cgh_plan_set_loss(cgh_plan* plan, int32_t kind, const uint8_t* recon_mask);
 
 /* Synchronous status read of the last raster call on this plan (blocks on `stream`):
  * pairs_needed = (Gaussian, tile) pairs of the last binning, overflow = 1 if that

@@ -52,7 +52,8 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
            "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
            "cgh_autotune", "cgh_conv3x3_fwd", "cgh_conv3x3_bwd", "cgh_cast_bf16",
-           "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad", "cgh_measure_peaks")
+           "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad", "cgh_measure_peaks",
+           "cgh_plan_set_loss")
 
 
 def library_path() -> str:
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_encoder_decode_bwd.argtypes = [i32, i32, i32, i32, i32, i32, i32,
                                            ctypes.POINTER(_Grads), vp, vp]
     lib.cgh_mse_grad.argtypes = [i64, vp, vp, f32, i32, vp, vp, vp]
+    lib.cgh_plan_set_loss.argtypes = [vp, i32, vp]
     lib.cgh_measure_peaks.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(f64), vp]
     lib.cgh_launch_count.restype = i64
     lib.cgh_last_error_string.restype = ctypes.c_char_p
@@ -226,6 +228,16 @@ class Plan:
         _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
         if self._ws is not None:
             self._attach_workspace()
+
+    def set_loss(self, kind: str = "mse", mask=None):
+        """cgh_plan_set_loss: 'mse' (L_MSE) or 'recon' (three-term L_recon with the binary
+        depth masks `mask`, a CUDA uint8 tensor [L, H, W], or None for M = 0)."""
+        k = {"mse": 0, "recon": 1}[kind]
+        if mask is not None:
+            _need(mask, torch.uint8, (self.L, self.H, self.W), "mask")
+        self._mask = mask  # the plan reads it at every later call
+        _check(_lib.cgh_plan_set_loss(self._h, k, ctypes.c_void_p(mask.data_ptr()) if mask is not None
+                                      else ctypes.c_void_p(0)), "cgh_plan_set_loss")
 
     def get_tuning(self) -> dict:
         t = _Tuning()

@@ -159,6 +159,8 @@ extern "C" cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L
   bl.inv_ntot = (float)(1.0 / ((double)Ny * (double)Nx));
   bl.aperture2 = (float)(aperture * aperture);
   bl.series_ok = 1;
+  bl.loss_kind = 0;
+  bl.recon_mask = nullptr;
   for (int c = 0; c < C; ++c) {  // largest q = lambda^2 (fx^2 + fy^2) on the padded grid
     const double fxn = (double)(Nx / 2) / ((double)Nx * pitch_m);
     const double fyn = (double)(Ny / 2) / ((double)Ny * pitch_m);
@@ -326,6 +328,15 @@ extern "C" cgh_status cgh_plan_band_limits(const cgh_plan* plan, int32_t* kx_max
     kx_max[i] = plan->bl.tf[i].kx_max;
     ky_max[i] = plan->bl.tf[i].ky_max;
   }
+  return CGH_OK;
+}
+
+extern "C" cgh_status cgh_plan_set_loss(cgh_plan* plan, int32_t kind, const uint8_t* recon_mask) {
+  if (!plan) return fail(CGH_ERR_ARG, "plan is NULL");
+  if (kind != CGH_LOSS_MSE && kind != CGH_LOSS_RECON) return fail(CGH_ERR_ARG, "unknown loss kind");
+  if (kind == CGH_LOSS_MSE && recon_mask) return fail(CGH_ERR_ARG, "a depth mask needs CGH_LOSS_RECON");
+  plan->bl.loss_kind = kind;
+  plan->bl.recon_mask = recon_mask;
   return CGH_OK;
 }
 

@@ -149,9 +149,11 @@ __global__ void __launch_bounds__(512, 1) k_rows_loss(const __grid_constant__ Bl
     if (x >= 0 && x < W) {
       const float2 u = sm[a];
       const float I = fmaf(u.x, u.x, u.y * u.y);
-      const float d = I - tg[(size_t)(y0 + b) * W + x];
-      acc = fmaf(d, d, acc);
-      g = cscale(u, gscale * d);
+      const float t = tg[(size_t)(y0 + b) * W + x];
+      const float d = I - t;
+      const float wd = loss_weight(bl, batch / bl.C, y0 + b, x, t) * d;
+      acc = fmaf(wd, d, acc);
+      g = cscale(u, gscale * wd);
     }
     sm[a] = g;
   }
@@ -205,17 +207,22 @@ __global__ void __launch_bounds__(512, 1) k_cols_bwd_planes(const __grid_constan
 }
 
 // Unfused intensity loss for the standalone API: partials per block, optional gradient.
-__global__ void k_loss_pointwise(long long total, float gscale, const float2* __restrict__ Ud,
+__global__ void k_loss_pointwise(const __grid_constant__ BlasmDev bl, long long total,
+                                 float gscale, const float2* __restrict__ Ud,
                                  const float* __restrict__ target, float* __restrict__ partials,
                                  float2* __restrict__ dUd) {
   __shared__ float red[32];
   float acc = 0.f;
+  const long long HW = (long long)bl.H * bl.W;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const float2 u = Ud[i];
-    const float d = fmaf(u.x, u.x, u.y * u.y) - target[i];
-    acc = fmaf(d, d, acc);
-    if (dUd) dUd[i] = cscale(u, gscale * d);
+    const float t = target[i];
+    const float d = fmaf(u.x, u.x, u.y * u.y) - t;
+    const long long lc = i / HW, r = i - lc * HW;  // i = ((l C + c) H + y) W + x
+    const float wd = loss_weight(bl, (int)(lc / bl.C), (int)(r / bl.W), (int)(r % bl.W), t) * d;
+    acc = fmaf(wd, d, acc);
+    if (dUd) dUd[i] = cscale(u, gscale * wd);
   }
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
@@ -425,8 +432,8 @@ cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* ta
   const long long total = (long long)p->L * p->C * p->H * p->W;
   const float gscale = 4.0f / (float)total;
   prof_begin(KID_LOSS_POINTWISE, s);
-  k_loss_pointwise<<<pointwise_loss_blocks(p), 256, 0, s>>>(total, gscale, Ud, target, partials,
-                                                           dUd);
+  k_loss_pointwise<<<pointwise_loss_blocks(p), 256, 0, s>>>(p->bl, total, gscale, Ud, target,
+                                                           partials, dUd);
   prof_end(KID_LOSS_POINTWISE, s);
   return cudaGetLastError();
 }

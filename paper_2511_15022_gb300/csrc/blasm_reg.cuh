@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
       const float I_ = fmaf(val.x, val.x, val.y * val.y);
       const float t_ = tstage ? tsm[b * W + x] : __ldg(&tg[(size_t)y * W + x]);
       const float d = I_ - t_;
-      acc = fmaf(d, d, acc);
-      val = cscale(val, gscale * d);
+      const float wd = loss_weight(bl, batch / bl.C, y, x, t_) * d;
+      acc = fmaf(wd, d, acc);
+      val = cscale(val, gscale * wd);
     } else {
       val = make_float2(0.f, 0.f);
     }

@@ -49,9 +49,19 @@ struct BlasmDev {
   int oy, ox;      // offset of the image window inside the padded grid
   float inv_ntot;  // 1 / (Ny * Nx)
   float aperture2; // aperture radius^2 in index units (0 = off)
-  int series_ok;   // every bin has q = lambda^2 (fx^2 + fy^2) < 0.05 (see transfer_series)
+  int series_ok;   // every bin has q = lambda^2 (fx^2 + fy^2) < 0.04 (see transfer_series)
+  int loss_kind;   // 0: intensity MSE; 1: three-term L_recon (Sec. 3.2)
+  const unsigned char* recon_mask;  // L_recon depth masks [L][H][W] (NULL: M = 0)
   TFConst tf[CGH_MAX_C * CGH_MAX_L];  // index c * L + l
 };
+
+// Per-pixel weight of the loss: (I - T)^2 w.  The three-term L_recon of Sec. 3.2 is
+// (I - T)^2 + (I M - T M)^2 + (I T - T T)^2 = (I - T)^2 (1 + M + T^2) for binary M.
+__device__ __forceinline__ float loss_weight(const BlasmDev& bl, int l, int y, int x, float t) {
+  if (bl.loss_kind == 0) return 1.f;
+  const float m = bl.recon_mask ? (bl.recon_mask[((size_t)l * bl.H + y) * bl.W + x] ? 1.f : 0.f) : 0.f;
+  return 1.f + m + t * t;
+}
 
 struct cgh_plan {
   // geometry and optics

@@ -182,3 +182,22 @@ def planted_scene(N: int, C: int, H: int, W: int, seed: int, blobs: int = 8,
     p["amp"] = amp
     p["phase"] = np.zeros((N, C))
     return {k: np.ascontiguousarray(v.astype(dtype)) for k, v in p.items()}
+
+
+def depth_masks(L: int, H: int, W: int, seed: int, blobs: int = 6) -> np.ndarray:
+    """Binary depth masks [L, H, W] uint8 for the reconstruction loss: a smooth synthetic
+    depth map (sum of isotropic blobs, sigma U(H/8, H/3)) normalised to [0, 1) and
+    quantised into L levels; mask l marks the pixels whose depth falls in level l (the
+    paper's masks come from a depth estimator, which is not available here)."""
+    rng = np.random.default_rng(seed)
+    yy = np.arange(H, dtype=np.float64)[:, None]
+    xx = np.arange(W, dtype=np.float64)[None, :]
+    depth = np.zeros((H, W))
+    for _ in range(blobs):
+        cx, cy = rng.uniform(0, W), rng.uniform(0, H)
+        sig = rng.uniform(H / 8.0, H / 3.0)
+        depth += rng.uniform(0.2, 1.0) * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig * sig))
+    lo, hi = depth.min(), depth.max()
+    depth = (depth - lo) / (hi - lo + 1e-12) * (1.0 - 1e-9)
+    q = np.minimum((depth * L).astype(np.int64), L - 1)
+    return np.stack([(q == l).astype(np.uint8) for l in range(L)])
