@@ -385,6 +385,79 @@ def recon_bench(dev, plan_tuning=None, steps: int = 20) -> dict:
             "what": "fused step + Adam; L_recon weight 1 + M + T^2 applied in the loss row pass"}
 
 
+# ------------------------------------------------------------------ POH conversion
+def poh_bench(dev, plan_tuning=None, iters: int = 300, phase_lr: float = 1e-2) -> dict:
+    """Random-POH conversion (Sec. 3.3) on the 1080p smooth blob targets: the Gaussians (plain
+    random initialisation) and a random phase field phi ~ U(-pi, pi) optimised jointly with
+    L_extract (lambda_comp 0.1, lambda_field 0.01, L_recon with synthetic depth masks) by
+    Adam (the paper's rates; phi at 1e-2).  A phase-only field has unit amplitude, so the
+    targets are scaled to mean intensity 1 (the intensity such a field carries).
+    Reports the joint step's time and the normalised RMS intensity error of the complex
+    hologram, of the random POH exp(j phi), of the smooth POH (DPAC of the Gaussians' field,
+    double-phase and as printed) and of a random phase field after `iters` iterations."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2511_15022_gb300 import cgh, inputs
+    w = inputs.hd_1080p()
+    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
+                    max_gaussians=w.N, device=dev)
+    if plan_tuning:
+        plan.set_tuning(**{k: v for k, v in plan_tuning.items() if k != "pair_capacity_per_gaussian"})
+    target = torch.from_numpy(inputs.blob_targets(w.L, w.C, w.H, w.W)).to(dev)
+    target = (target / target.mean()).contiguous()
+    mask = torch.from_numpy(inputs.depth_masks(w.L, w.H, w.W, seed=inputs.SEED_TARGETS)).to(dev)
+    plan.set_loss("recon", mask)
+    p = {k: torch.from_numpy(v).to(dev) for k, v in inputs.params_for(w).items()}
+    gen = torch.Generator(device=dev).manual_seed(inputs.SEED_PLANTED)
+    phi = (torch.rand((w.C, w.H, w.W), generator=gen, device=dev) * 2 - 1) * math.pi
+    g = plan.empty_grads(w.N)
+    dphi = torch.empty_like(phi)
+    state = {k: (torch.zeros_like(v), torch.zeros_like(v)) for k, v in list(p.items()) + [("phi", phi)]}
+    loss = torch.empty(1, device=dev)
+    it = [0]
+
+    def one():
+        plan.poh_step(p, phi, target, 0.1, 0.01, grads=g, dphi=dphi, loss_out=loss)
+        it[0] += 1
+        groups = [(p[k], g[k], state[k][0], state[k][1], LRS[k]) for k in cgh.PARAM_KEYS]
+        groups.append((phi, dphi, state["phi"][0], state["phi"][1], phase_lr))
+        cgh.adam_step(groups, it[0])
+
+    tmean = float(target.mean())
+
+    def nrmse(field):  # RMS intensity error over the mean target intensity, all planes
+        with torch.no_grad():
+            Ip = plan.blasm_fwd(field).abs().square()
+            return round(float(((Ip - target) ** 2).mean().sqrt()) / tmean, 4)
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters - 3):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (iters - 3)
+    U0 = plan.raster_fwd(p)
+    out = {"ms_per_step": ms, "it_per_s": 1000.0 / ms, "iterations": iters,
+           "nrmse": {"complex_hologram": nrmse(U0), "random_poh": nrmse(plan.poh_field(phi)),
+                     "smooth_poh_double_phase": nrmse(plan.poh_dpac(U0, mode="double")),
+                     "smooth_poh_as_printed": nrmse(plan.poh_dpac(U0, mode="printed")),
+                     "random_phase_baseline": nrmse(plan.poh_field(
+                         (torch.rand((w.C, w.H, w.W), generator=gen, device=dev) * 2 - 1) * math.pi))},
+           "target": ("smooth blob targets scaled to mean intensity 1; nrmse = RMS "
+                      "intensity error / mean target intensity over all planes"),
+           "what": ("joint step (raster, two BLASM forwards, L_extract, two adjoints, raster "
+                    "backward, phase gradient) + Adam over Gaussians and phi; 1080p RGB 3 planes")}
+    plan.close()
+    return out
+
+
 # ------------------------------------------------------------------ 4K stress
 def stress_4k(dev, steps: int = 5, warmup: int = 2) -> dict:
     """2160 x 3840 RGB hologram, 1M Gaussians (scales 0.3-8 px), 6 planes z ~ U[0, 20] mm:
@@ -874,6 +947,7 @@ def main():
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
             line["stress_4k"] = stress_4k(dev)
             line["l_recon"] = recon_bench(dev, plan_tuning=tuned)
+            line["poh_conversion"] = poh_bench(dev, plan_tuning=tuned)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

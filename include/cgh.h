@@ -306,6 +306,39 @@ cgh_status cgh_encoder_decode_bwd(int32_t B, int32_t CY, int32_t CX, int32_t S, 
                                   int32_t H, int32_t W, const cgh_grads* param_grads,
                                   float* dout, void* stream);
 
+/* ---- phase-only hologram (POH) conversion (Sec. 3.3) ----
+ *
+ * cgh_poh_dpac: smooth POH by checkerboard multiplexing (DPAC).  With A = |U0| and
+ *   phi = arg U0 per channel and pixel (row i, column j):
+ *   mode 1, double-phase amplitude coding (the method the paper cites): phi_DPAC = phi +
+ *     acos(A / max_c A) where i + j is even and phi - acos(A / max_c A) where it is odd
+ *     (max over the channel's pixels), so each neighbouring pair averages to U0 / max A;
+ *   mode 0, the formula as printed: phi_DPAC = A where i + j is even, phi where odd.
+ *   H_out = exp(j phi_DPAC).  U0, H_out: DEVICE complex64 [C][H][W] of the plan's size; uses
+ *   the plan's workspace for the per-channel maxima. */
+cgh_status cgh_poh_dpac(const cgh_plan* plan, const void* U0, void* H_out, int32_t mode,
+                        void* stream);
+
+/* H_out = exp(j phi): the random POH of a phase field phi (DEVICE float [C][H][W]). */
+cgh_status cgh_poh_field(const cgh_plan* plan, const float* phi, void* H_out, void* stream);
+
+/* Scratch (caller-owned device memory) needed by cgh_poh_step: (2 L C + C) H W complex64. */
+cgh_status cgh_poh_scratch_bytes(const cgh_plan* plan, size_t* bytes);
+
+/* One joint forward + backward pass of the random-POH conversion (Sec. 3.3): the Gaussians'
+ * field H and the random POH exp(j phi) are both propagated to the L planes and
+ *   L_extract = sum_l [ R_l(I_l) + R_l(I_rand,l) + lambda_comp mean (I_l - I_rand,l)^2
+ *               + lambda_field mean (|Re(U(d_l) - U_rand(d_l))| + |Im(U(d_l) - U_rand(d_l))|) ]
+ * is written to loss_out (device float[1]), with R_l plane l's part of L_recon (the plan's
+ * depth masks, cgh_plan_set_loss; M = 0 without them) and every mean over the C H W values
+ * of one plane (the paper uses lambda_comp = 0.1, lambda_field = 0.01).  Gradients of the
+ * Gaussian parameters go to grads (overwritten), dL/dphi to dphi (DEVICE float [C][H][W],
+ * overwritten).  scratch: at least cgh_poh_scratch_bytes bytes of device memory. */
+cgh_status cgh_poh_step(cgh_plan* plan, const cgh_params* params, const float* phi,
+                        const float* target, float lambda_comp, float lambda_field,
+                        float* loss_out, const cgh_grads* grads, float* dphi, void* scratch,
+                        size_t scratch_bytes, void* stream);
+
 /* Measurement utility (no counterpart in the paper): FP32 FMA throughput (flop/s, one FMA
  * = 2 flops) and MUFU throughput (special-function operations/s) of the current device,
  * from two microbenchmark kernels timed with CUDA events on `stream` (synchronous, ~50 ms).

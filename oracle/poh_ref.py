@@ -1,9 +1,10 @@
 """FP64 CPU oracle for the phase-only hologram (POH) conversion of Sec. 3.3.  TEST
 INFRASTRUCTURE ONLY (see oracle/__init__.py for who may import it).
 
-* Smooth POH (double-phase amplitude coding, as the paper prints it): with A = |H| and
-  phi = arg H per channel and pixel, phi_DPAC(i, j) = A(i, j) where i + j is even and
-  phi(i, j) where it is odd; H_smooth = exp(j phi_DPAC).
+* Smooth POH by double-phase amplitude coding (DPAC, the method the paper cites): with
+  A_n = |H| / max |H| per channel and phi = arg H, phi_DPAC = phi + acos(A_n) where i + j is
+  even and phi - acos(A_n) where it is odd; H_smooth = exp(j phi_DPAC).  The formula the
+  paper prints (A where i + j is even, phi where odd) is kept as mode "printed".
 * Random POH: H_rand = exp(j phi_rand) with a learnable phase field phi_rand [C, H, W],
   propagated beside the Gaussians' field H; the joint objective is
     L_extract = sum_l [ R_l(I_l) + R_l(I_rand,l) + lambda_comp mean (I_l - I_rand,l)^2
@@ -25,14 +26,24 @@ import numpy as np
 import oracle
 
 
-def dpac(Hf):
-    """Smooth POH of a complex field [C, H, W]: exp(j phi_DPAC) (Sec. 3.3)."""
+def dpac(Hf, mode: str = "double"):
+    """Smooth POH of a complex field [C, H, W]: exp(j phi_DPAC) (Sec. 3.3).
+    mode "double": double-phase amplitude coding, the method the paper cites -- with
+    A_n = |H| / max|H| per channel and phi = arg H, phi_DPAC = phi + acos(A_n) where i + j
+    is even and phi - acos(A_n) where it is odd (each neighbouring pair averages to
+    A_n exp(j phi)).  mode "printed": the formula as printed, A where i + j is even and phi
+    where it is odd."""
     Hf = np.asarray(Hf, np.complex128)
     C, H, W = Hf.shape
     A = np.abs(Hf)
     phi = np.angle(Hf)
     even = ((np.arange(H)[:, None] + np.arange(W)[None, :]) % 2) == 0
-    pd = np.where(even[None], A, phi)
+    if mode == "printed":
+        pd = np.where(even[None], A, phi)
+    else:
+        amax = A.reshape(C, -1).max(axis=1)[:, None, None]
+        a = np.arccos(np.clip(A / np.where(amax > 0, amax, 1.0), 0.0, 1.0))
+        pd = np.where(even[None], phi + a, phi - a)
     return np.exp(1j * pd)
 
 

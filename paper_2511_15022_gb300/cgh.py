@@ -53,7 +53,8 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
            "cgh_autotune", "cgh_conv3x3_fwd", "cgh_conv3x3_bwd", "cgh_cast_bf16",
            "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad", "cgh_measure_peaks",
-           "cgh_plan_set_loss")
+           "cgh_plan_set_loss", "cgh_poh_dpac", "cgh_poh_field", "cgh_poh_scratch_bytes",
+           "cgh_poh_step")
 
 
 def library_path() -> str:
@@ -111,6 +112,11 @@ def load(build_if_missing: bool = True):
                                            ctypes.POINTER(_Grads), vp, vp]
     lib.cgh_mse_grad.argtypes = [i64, vp, vp, f32, i32, vp, vp, vp]
     lib.cgh_plan_set_loss.argtypes = [vp, i32, vp]
+    lib.cgh_poh_dpac.argtypes = [vp, vp, vp, i32, vp]
+    lib.cgh_poh_field.argtypes = [vp, vp, vp, vp]
+    lib.cgh_poh_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cgh_poh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, f32, f32, vp,
+                                 ctypes.POINTER(_Grads), vp, vp, ctypes.c_size_t, vp]
     lib.cgh_measure_peaks.argtypes = [ctypes.POINTER(f64), ctypes.POINTER(f64), vp]
     lib.cgh_launch_count.restype = i64
     lib.cgh_last_error_string.restype = ctypes.c_char_p
@@ -228,6 +234,51 @@ class Plan:
         _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
         if self._ws is not None:
             self._attach_workspace()
+
+    # -- phase-only hologram conversion (Sec. 3.3)
+    def poh_dpac(self, U0, mode: str = "double", out=None, stream=None) -> torch.Tensor:
+        """cgh_poh_dpac: smooth POH exp(j phi_DPAC) of a complex field [C, H, W]; mode
+        'double' (double-phase amplitude coding) or 'printed' (the formula as printed)."""
+        _need(U0, torch.complex64, (self.C, self.H, self.W), "U0")
+        out = out if out is not None else torch.empty_like(U0)
+        _need(out, torch.complex64, (self.C, self.H, self.W), "H_out")
+        _check(_lib.cgh_poh_dpac(self._h, ctypes.c_void_p(U0.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), {"printed": 0, "double": 1}[mode],
+                                 ctypes.c_void_p(_stream(stream))), "cgh_poh_dpac")
+        return out
+
+    def poh_field(self, phi, out=None, stream=None) -> torch.Tensor:
+        """cgh_poh_field: exp(j phi) for a phase field [C, H, W]."""
+        _need(phi, torch.float32, (self.C, self.H, self.W), "phi")
+        out = out if out is not None else torch.empty(phi.shape, dtype=torch.complex64,
+                                                      device=phi.device)
+        _check(_lib.cgh_poh_field(self._h, ctypes.c_void_p(phi.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream(stream))),
+               "cgh_poh_field")
+        return out
+
+    def poh_step(self, params, phi, target, lambda_comp=0.1, lambda_field=0.01, grads=None,
+                 dphi=None, loss_out=None, stream=None):
+        """cgh_poh_step: joint random-POH conversion pass.  Returns (loss, grads, dphi)."""
+        prm = self._params(params)
+        _need(phi, torch.float32, (self.C, self.H, self.W), "phi")
+        _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
+        g = grads if grads is not None else self.empty_grads(prm.N)
+        gs = self._grads(g, prm.N)
+        dphi = dphi if dphi is not None else torch.empty_like(phi)
+        _need(dphi, torch.float32, (self.C, self.H, self.W), "dphi")
+        loss = loss_out if loss_out is not None else torch.empty(1, device=self.device)
+        n = ctypes.c_size_t()
+        _check(_lib.cgh_poh_scratch_bytes(self._h, ctypes.byref(n)), "cgh_poh_scratch_bytes")
+        if getattr(self, "_poh_scratch", None) is None or self._poh_scratch.numel() < n.value:
+            self._poh_scratch = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        _check(_lib.cgh_poh_step(self._h, ctypes.byref(prm), ctypes.c_void_p(phi.data_ptr()),
+                                 ctypes.c_void_p(target.data_ptr()), float(lambda_comp),
+                                 float(lambda_field), ctypes.c_void_p(loss.data_ptr()),
+                                 ctypes.byref(gs), ctypes.c_void_p(dphi.data_ptr()),
+                                 ctypes.c_void_p(self._poh_scratch.data_ptr()), n.value,
+                                 ctypes.c_void_p(_stream(stream))), "cgh_poh_step")
+        return loss, g, dphi
 
     def set_loss(self, kind: str = "mse", mask=None):
         """cgh_plan_set_loss: 'mse' (L_MSE) or 'recon' (three-term L_recon with the binary

@@ -438,6 +438,14 @@ cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* ta
   return cudaGetLastError();
 }
 
+cudaError_t launch_loss_finalize_scaled(const float* partials, int count, double inv, float* out,
+                                        cudaStream_t s) {
+  prof_begin(KID_LOSS_FINALIZE, s);
+  k_loss_finalize<<<1, 1024, 0, s>>>(partials, count, inv, out);
+  prof_end(KID_LOSS_FINALIZE, s);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_loss_finalize(cgh_plan* p, const float* partials, int count, float* out,
                                  cudaStream_t s) {
   const double inv = 1.0 / ((double)p->L * p->C * p->H * p->W);

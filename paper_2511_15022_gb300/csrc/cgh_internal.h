@@ -122,6 +122,9 @@ cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* ta
                                   float* partials, float2* dUd, cudaStream_t s);
 cudaError_t launch_loss_finalize(cgh_plan* p, const float* partials, int count, float* out,
                                  cudaStream_t s);
+// sum(partials) * inv (FP64, fixed order) -> out[0]
+cudaError_t launch_loss_finalize_scaled(const float* partials, int count, double inv, float* out,
+                                        cudaStream_t s);
 int rows_loss_blocks(const cgh_plan* p);
 int pointwise_loss_blocks(const cgh_plan* p);
 // api.cu
@@ -138,7 +141,7 @@ enum KernelId {
   KID_PREPROCESS = 0, KID_SCAN_TILES, KID_EMIT, KID_RASTER_FWD, KID_RASTER_BWD,
   KID_GRAD_FINALIZE, KID_ROWS_PAD_FWD, KID_COLS_FWD_PLANES, KID_ROWS_LOSS,
   KID_COLS_BWD_PLANES, KID_ROWS_INV_CROP, KID_LOSS_POINTWISE, KID_LOSS_FINALIZE, KID_ADAM,
-  KID_ENCODER, KID_COUNT
+  KID_ENCODER, KID_POH, KID_COUNT
 };
 // Bracket one kernel launch: records a CUDA event before and after it on its stream when
 // profiling is enabled; otherwise only the launch counter moves.

@@ -8,11 +8,11 @@ import oracle
 from oracle import poh_ref as pr
 
 
-def test_dpac_of_a_constant_field_is_a_checkerboard():
+def test_dpac_printed_form_of_a_constant_field_is_a_checkerboard():
     a, th = 0.7, -1.2
     H, W = 6, 8
     Hf = np.full((1, H, W), a * np.exp(1j * th))
-    out = pr.dpac(Hf)
+    out = pr.dpac(Hf, mode="printed")
     assert np.allclose(np.abs(out), 1.0)
     F = np.fft.fft2(out[0])
     n = H * W
@@ -21,6 +21,21 @@ def test_dpac_of_a_constant_field_is_a_checkerboard():
     rest = np.abs(F).copy()
     rest[0, 0] = rest[H // 2, W // 2] = 0.0
     assert rest.max() < 1e-12
+
+
+def test_double_phase_pairs_average_to_the_normalised_field():
+    """cos-addition: (exp(j(phi + a)) + exp(j(phi - a))) / 2 = cos(a) exp(j phi), so on a
+    field constant over horizontal pixel pairs every pair of the coded field averages to
+    (|H| / max|H|) exp(j arg H)."""
+    rng = np.random.default_rng(9)
+    C, H, W = 2, 4, 6
+    half = rng.uniform(0.1, 2.0, size=(C, H, W // 2)) * np.exp(1j * rng.uniform(-3, 3, size=(C, H, W // 2)))
+    Hf = np.repeat(half, 2, axis=2)
+    out = pr.dpac(Hf)
+    assert np.allclose(np.abs(out), 1.0)
+    pair_mean = 0.5 * (out[:, :, 0::2] + out[:, :, 1::2])
+    amax = np.abs(half).reshape(C, -1).max(axis=1)[:, None, None]
+    assert np.abs(pair_mean - half / amax).max() < 1e-12
 
 
 def _fields(seed, L=2, C=2, H=4, W=5):
