@@ -22,6 +22,11 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                 count from the closed form, adjoint dot-product identity.
   mse_loss/psnr pinned: closed forms, finite differences.
   adam          pinned: hand-iterated scalar recurrence, torch.optim.Adam (CPU).
+  recon_loss    pinned: sum of three intensity MSEs of transformed inputs (through the pinned
+                mse_loss), finite differences, closed form, no-mask case.
+  adan          pinned: equals the pinned Adam with beta2 = 0, constant-gradient closed
+                form, gradient-scale invariance, weight decay.
+  (encoder_ref.py and poh_ref.py carry their own pin lists.)
 """
 from __future__ import annotations
 
@@ -80,6 +85,7 @@ def _load():
         lib.orc_psnr.argtypes = [i, i, i, i, _dp, _dp]
         lib.orc_psnr.restype = d
         lib.orc_adam.argtypes = [i64, _dp, _dp, _dp, _dp, d, d, d, d, i]
+        lib.orc_adan.argtypes = [i64, _dp, _dp, _dp, _dp, _dp, _dp, d, d, d, d, d, d, i]
         lib.orc_num_threads.restype = i
         lib.orc_set_num_threads.argtypes = [i]
         _lib = lib
@@ -272,6 +278,17 @@ def adam(p, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
     g = _f64(g)
     _load().orc_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), float(lr), float(beta1),
                      float(beta2), float(eps), int(t))
+
+
+def adan(p, g, m, v, n, gprev, lr, t, beta1=0.98, beta2=0.92, beta3=0.99, eps=1e-8,
+         weight_decay=0.0):
+    """One in-place Adan step (Sec. 4's optimiser) on float64 arrays p, m, v, n, gprev."""
+    for a in (p, m, v, n, gprev):
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == p.shape
+    g = _f64(g)
+    _load().orc_adan(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), _ptr(n), _ptr(gprev),
+                     float(lr), float(beta1), float(beta2), float(beta3), float(eps),
+                     float(weight_decay), int(t))
 
 
 def forward(params: dict, H: int, W: int, lambdas, pitch: float, z, pad: int = 2,

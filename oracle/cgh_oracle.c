@@ -543,6 +543,31 @@ double orc_psnr(int L, int C, int H, int W, const double* Ud, const double* targ
     return sum / (double)L;
 }
 
+/* Adan step (adaptive Nesterov momentum; the optimiser the paper trains with, Sec. 4),
+ * restated from its published algorithm with the bias corrections of the authors' release,
+ * betas in the "running average" convention (defaults 0.98, 0.92, 0.99):
+ *   d = g - g_prev (d = 0 at t = 1)
+ *   m = b1 m + (1 - b1) g;   v = b2 v + (1 - b2) d;   n = b3 n + (1 - b3) (g + b2 d)^2
+ *   p = (p - lr (m / (1 - b1^t) + b2 v / (1 - b2^t)) / (sqrt(n / (1 - b3^t)) + eps))
+ *       / (1 + lr wd);   g_prev = g.  Step t >= 1. */
+void orc_adan(int64_t n, double* p, const double* g, double* m, double* v, double* nn,
+              double* gprev, double lr, double b1, double b2, double b3, double eps,
+              double wd, int t) {
+    double bc1 = 1.0 - pow(b1, (double)t);
+    double bc2 = 1.0 - pow(b2, (double)t);
+    double bc3 = 1.0 - pow(b3, (double)t);
+    for (int64_t i = 0; i < n; ++i) {
+        double d = (t == 1) ? 0.0 : g[i] - gprev[i];
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * d;
+        double u = g[i] + b2 * d;
+        nn[i] = b3 * nn[i] + (1.0 - b3) * u * u;
+        double step = (m[i] / bc1 + b2 * v[i] / bc2) / (sqrt(nn[i] / bc3) + eps);
+        p[i] = (p[i] - lr * step) / (1.0 + lr * wd);
+        gprev[i] = g[i];
+    }
+}
+
 /* Adam step with PyTorch semantics (no weight decay, no amsgrad), step t >= 1. */
 void orc_adam(int64_t n, double* p, const double* g, double* m, double* v, double lr,
               double beta1, double beta2, double eps, int t) {
