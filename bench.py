@@ -557,7 +557,7 @@ def batched_bench(dev, steps: int, warmup: int) -> dict:
 
 # ------------------------------------------------------------------ time to target PSNR
 def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_every: int = 10,
-                 plan_tuning=None) -> dict:
+                 plan_tuning=None, optimizer: str = "adam") -> dict:
     """Plain method (random initialisation, Adam with the paper's per-group learning rates,
     position rate cosine-annealed 1e-2 -> 1e-3) on a planted target: seed-999 Gaussians of
     the same distributions rendered and propagated by this library, amplitudes scaled so the
@@ -594,7 +594,8 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
     target = plan.blasm_fwd(plan.raster_fwd(planted)).abs().square().contiguous()
     params = {k: torch.from_numpy(v).to(dev).requires_grad_(True)
               for k, v in inputs.params_for(w).items()}
-    state = {k: (torch.zeros_like(v), torch.zeros_like(v)) for k, v in params.items()}
+    nstate = 4 if optimizer == "adan" else 2
+    state = {k: tuple(torch.zeros_like(v) for _ in range(nstate)) for k, v in params.items()}
 
     def psnr():
         with torch.no_grad():
@@ -616,8 +617,12 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
             for k in params:
                 params[k].grad = None
             hologram_loss(plan, params, target).backward()
-            cgh.adam_step([(params[k].data, params[k].grad, state[k][0], state[k][1],
-                            lr_pos if k == "xy_raw" else LRS[k]) for k in cgh.PARAM_KEYS], it)
+            groups = [(params[k].data, params[k].grad, *state[k], lr_pos if k == "xy_raw" else LRS[k])
+                      for k in cgh.PARAM_KEYS]
+            if optimizer == "adan":
+                cgh.adan_step(groups, it)
+            else:
+                cgh.adam_step(groups, it)
         torch.cuda.synchronize()
         elapsed += time.perf_counter() - t0
         db = psnr()
@@ -634,7 +639,7 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
             "best_db": max(h[1] for h in hist),
             "levels": {str(l): crossed.get(l) for l in levels},
             "iterations_run": it, "seconds_run": elapsed, "psnr_history": hist[::4] + hist[-1:],
-            "method": "plain (random init), autograd recompute path, Adam",
+            "method": f"plain (random init), autograd recompute path, {optimizer.capitalize()}",
             "initial_db": hist[0][1],
             "target": ("planted: seed-999 Gaussians, zero phases, amplitudes from a smooth blob "
                        "image, rendered and propagated; mean intensity 0.35, PSNR on [0, 1]-clipped "
@@ -944,6 +949,7 @@ def main():
         if not args.no_extras and world == 1:
             line["batched"] = batched_bench(dev, steps=max(5, args.steps // 4), warmup=3)
             line["time_to_psnr"] = time_to_psnr(dev, plan_tuning=tuned)
+            line["time_to_psnr_adan"] = time_to_psnr(dev, plan_tuning=tuned, optimizer="adan")
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
             line["stress_4k"] = stress_4k(dev)
             line["l_recon"] = recon_bench(dev, plan_tuning=tuned)

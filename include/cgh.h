@@ -221,6 +221,30 @@ typedef struct {
 cgh_status cgh_adam_step(const cgh_adam_group* groups /* host array */, int32_t num_groups,
                          int32_t step, float beta1, float beta2, float eps, void* stream);
 
+/* Adan (adaptive Nesterov momentum), the optimiser of Sec. 4, restated from its published
+ * algorithm with the bias corrections of the authors' release (betas as running-average
+ * weights; 0.98, 0.92, 0.99 are the usual values).  Per element, step t >= 1:
+ *   d = g - prev_grad (0 when t = 1); m = b1 m + (1-b1) g; v = b2 v + (1-b2) d;
+ *   n = b3 n + (1-b3) (g + b2 d)^2;
+ *   p = (p - lr (m/(1-b1^t) + b2 v/(1-b2^t)) / (sqrt(n/(1-b3^t)) + eps)) / (1 + lr wd);
+ *   prev_grad = g.
+ * Up to 8 groups (host array); all state arrays (exp_avg = m, exp_avg_diff = v,
+ * exp_avg_sq = n, prev_grad) are device float arrays of `count` elements, zero at t = 1. */
+typedef struct {
+  float* param;
+  const float* grad;
+  float* exp_avg;
+  float* exp_avg_diff;
+  float* exp_avg_sq;
+  float* prev_grad;
+  int64_t count;
+  float lr;
+} cgh_adan_group;
+
+cgh_status cgh_adan_step(const cgh_adan_group* groups, int32_t num_groups, int32_t step,
+                         float beta1, float beta2, float beta3, float eps, float weight_decay,
+                         void* stream);
+
 /* Adam over any number of parameter groups in one launch: groups_dev is a DEVICE array of
  * num_groups cgh_adam_group records, offsets_dev a DEVICE array of num_groups + 1 int64
  * prefix sums of their counts (offsets_dev[num_groups] = total).  Same update as

@@ -37,6 +37,13 @@ class _Tuning(ctypes.Structure):
                 ("fft_kernels", ctypes.c_int32)]
 
 
+class _AdanGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+                ("exp_avg", ctypes.c_void_p), ("exp_avg_diff", ctypes.c_void_p),
+                ("exp_avg_sq", ctypes.c_void_p), ("prev_grad", ctypes.c_void_p),
+                ("count", ctypes.c_int64), ("lr", ctypes.c_float)]
+
+
 class _AdamGroup(ctypes.Structure):
     _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p),
                 ("exp_avg", ctypes.c_void_p), ("exp_avg_sq", ctypes.c_void_p),
@@ -54,7 +61,7 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_autotune", "cgh_conv3x3_fwd", "cgh_conv3x3_bwd", "cgh_cast_bf16",
            "cgh_encoder_decode", "cgh_encoder_decode_bwd", "cgh_mse_grad", "cgh_measure_peaks",
            "cgh_plan_set_loss", "cgh_poh_dpac", "cgh_poh_field", "cgh_poh_scratch_bytes",
-           "cgh_poh_step")
+           "cgh_poh_step", "cgh_adan_step")
 
 
 def library_path() -> str:
@@ -112,6 +119,7 @@ def load(build_if_missing: bool = True):
                                            ctypes.POINTER(_Grads), vp, vp]
     lib.cgh_mse_grad.argtypes = [i64, vp, vp, f32, i32, vp, vp, vp]
     lib.cgh_plan_set_loss.argtypes = [vp, i32, vp]
+    lib.cgh_adan_step.argtypes = [ctypes.POINTER(_AdanGroup), i32, i32, f32, f32, f32, f32, f32, vp]
     lib.cgh_poh_dpac.argtypes = [vp, vp, vp, i32, vp]
     lib.cgh_poh_field.argtypes = [vp, vp, vp, vp]
     lib.cgh_poh_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
@@ -463,6 +471,23 @@ def adam_step(groups, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
                             float(lr))
     _check(lib.cgh_adam_step(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
                              ctypes.c_void_p(_stream(stream))), "cgh_adam_step")
+
+
+def adan_step(groups, step: int, beta1=0.98, beta2=0.92, beta3=0.99, eps=1e-8,
+              weight_decay=0.0, stream=None):
+    """Adan over up to 8 groups (cgh_adan_step): each group is
+    (param, grad, exp_avg, exp_avg_diff, exp_avg_sq, prev_grad, lr)."""
+    lib = load()
+    arr = (_AdanGroup * len(groups))()
+    for i, (p, g, m, v, n, gp, lr) in enumerate(groups):
+        for t, name in ((p, "param"), (g, "grad"), (m, "exp_avg"), (v, "exp_avg_diff"),
+                        (n, "exp_avg_sq"), (gp, "prev_grad")):
+            _need(t, torch.float32, tuple(p.shape), name)
+        arr[i] = _AdanGroup(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), n.data_ptr(),
+                            gp.data_ptr(), p.numel(), float(lr))
+    _check(lib.cgh_adan_step(arr, len(groups), int(step), float(beta1), float(beta2),
+                             float(beta3), float(eps), float(weight_decay),
+                             ctypes.c_void_p(_stream(stream))), "cgh_adan_step")
 
 
 class AdamTable:

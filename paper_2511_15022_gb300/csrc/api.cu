@@ -548,6 +548,87 @@ extern "C" cgh_status cgh_adam_step(const cgh_adam_group* groups, int32_t num_gr
   return CGH_OK;
 }
 
+// ------------------------------------------------------------------ Adan
+namespace {
+struct AdanArgs {
+  float* p[8];
+  const float* g[8];
+  float* m[8];
+  float* v[8];
+  float* n[8];
+  float* gp[8];
+  long long off[9];
+  float lr[8];
+  int ngroups;
+};
+
+// d = g - g_prev (0 at step 1); m, v, n running averages; bias-corrected step (see cgh.h)
+__global__ void k_adan(AdanArgs a, float b1, float b2, float b3, float eps, float wd, int first,
+                       float inv_bc1, float b2_over_bc2, float inv_sqrt_bc3) {
+  const long long total = a.off[a.ngroups];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int gi = 0;
+    while (i >= a.off[gi + 1]) ++gi;
+    const long long j = i - a.off[gi];
+    const float g = a.g[gi][j];
+    const float d = first ? 0.f : g - a.gp[gi][j];
+    const float m = fmaf(b1, a.m[gi][j], (1.f - b1) * g);
+    const float v = fmaf(b2, a.v[gi][j], (1.f - b2) * d);
+    const float u = fmaf(b2, d, g);
+    const float n = fmaf(b3, a.n[gi][j], (1.f - b3) * u * u);
+    a.m[gi][j] = m;
+    a.v[gi][j] = v;
+    a.n[gi][j] = n;
+    a.gp[gi][j] = g;
+    const float step = fmaf(m, inv_bc1, b2_over_bc2 * v) / fmaf(sqrtf(n), inv_sqrt_bc3, eps);
+    const float lr = a.lr[gi];
+    a.p[gi][j] = (a.p[gi][j] - lr * step) / fmaf(lr, wd, 1.f);
+  }
+}
+}  // namespace
+
+extern "C" cgh_status cgh_adan_step(const cgh_adan_group* groups, int32_t num_groups, int32_t step,
+                                    float beta1, float beta2, float beta3, float eps,
+                                    float weight_decay, void* stream) {
+  if (!groups || num_groups < 1 || num_groups > 8) return fail(CGH_ERR_ARG, "1..8 groups required");
+  if (step < 1) return fail(CGH_ERR_ARG, "step must be >= 1");
+  AdanArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ngroups = num_groups;
+  for (int i = 0; i < num_groups; ++i) {
+    const cgh_adan_group& g = groups[i];
+    if (g.count < 0) return fail(CGH_ERR_ARG, "group %d: negative count", i);
+    if (g.count > 0 && (!g.param || !g.grad || !g.exp_avg || !g.exp_avg_diff || !g.exp_avg_sq ||
+                        !g.prev_grad))
+      return fail(CGH_ERR_ARG, "group %d: NULL pointer", i);
+    a.p[i] = g.param;
+    a.g[i] = g.grad;
+    a.m[i] = g.exp_avg;
+    a.v[i] = g.exp_avg_diff;
+    a.n[i] = g.exp_avg_sq;
+    a.gp[i] = g.prev_grad;
+    a.lr[i] = g.lr;
+    a.off[i + 1] = a.off[i] + g.count;
+  }
+  for (int i = num_groups + 1; i < 9; ++i) a.off[i] = a.off[num_groups];
+  const long long total = a.off[num_groups];
+  if (total == 0) return CGH_OK;
+  const double bc1 = 1.0 - pow((double)beta1, (double)step);
+  const double bc2 = 1.0 - pow((double)beta2, (double)step);
+  const double bc3 = 1.0 - pow((double)beta3, (double)step);
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  cudaStream_t s = (cudaStream_t)stream;
+  prof_begin(KID_ADAM, s);
+  k_adan<<<(unsigned)blocks, 256, 0, s>>>(a, beta1, beta2, beta3, eps, weight_decay, step == 1,
+                                           (float)(1.0 / bc1), (float)((double)beta2 / bc2),
+                                           (float)(1.0 / sqrt(bc3)));
+  prof_end(KID_ADAM, s);
+  CGH_TRY(cudaGetLastError(), "cgh_adan_step");
+  return CGH_OK;
+}
+
 extern "C" int64_t cgh_launch_count(void) { return g_launches; }
 
 extern "C" const char* cgh_last_error_string(void) { return g_err; }
