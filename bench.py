@@ -458,6 +458,62 @@ def poh_bench(dev, plan_tuning=None, iters: int = 300, phase_lr: float = 1e-2) -
     return out
 
 
+# ------------------------------------------------------------------ render-latency sweep
+def render_sweep(dev, reps: int = 20) -> dict:
+    """Render latency against the parameter-reduction ratio (the setting of Table 3): a
+    3 x 640 x 1024 hologram (the paper's 3 x 1024 x 640 images), 3.74 um pitch,
+    639/532/473 nm, two planes at 1 and 5 mm (3 mm centre, 4 mm volume), N = 4.0M / (12
+    ratio) Gaussians.  'render' = raster forward + propagation to both planes (the
+    hologram and its reconstructions); the dense per-pixel row propagates a given per-pixel
+    field (no raster).  Also the fused optimisation step per ratio."""
+    import torch
+
+    from paper_2511_15022_gb300 import cgh, inputs
+    H, W = 640, 1024
+    wl, pitch, z = (639e-9, 532e-9, 473e-9), 3.74e-6, (1e-3, 5e-3)
+    dense_params = 3 * H * W * 2  # amplitude and phase per pixel and channel
+    out = {"setting": "3x640x1024, 3.74 um, 639/532/473 nm, planes 1 and 5 mm", "rows": []}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t = torch.from_numpy(inputs.blob_targets(len(z), 3, H, W)).to(dev)
+    for ratio in (None, 2, 3, 5, 7, 10):
+        N = 1 if ratio is None else int(round(dense_params / ratio / 12))
+        w = inputs.custom(H, W, N, wavelengths_m=wl, z_m=z, pitch_m=pitch, seed=inputs.SEED_GAUSSIANS + 7)
+        plan = cgh.Plan(H, W, wl, pitch, z, cutoff=w.cutoff, max_gaussians=N, device=dev)
+        if ratio is None:
+            U = torch.from_numpy(inputs.random_field(3, H, W, seed=3)).to(dev)
+            Ud = torch.empty(len(z), 3, H, W, dtype=torch.complex64, device=dev)
+            ms = timed(lambda: plan.blasm_fwd(U, out=Ud))
+            out["rows"].append({"ratio": "dense per-pixel", "params_M": dense_params / 1e6,
+                                "render_ms": round(ms, 3)})
+        else:
+            p = {k: torch.from_numpy(v).to(dev) for k, v in inputs.params_for(w).items()}
+            U = torch.empty(3, H, W, dtype=torch.complex64, device=dev)
+            Ud = torch.empty(len(z), 3, H, W, dtype=torch.complex64, device=dev)
+            ms = timed(lambda: plan.blasm_fwd(plan.raster_fwd(p, out=U), out=Ud))
+            g = plan.empty_grads(N)
+            loss = torch.empty(1, device=dev)
+            step_ms = timed(lambda: plan.step(p, t, grads=g, loss_out=loss))
+            out["rows"].append({"ratio": f"{ratio}:1", "gaussians": N,
+                                "params_M": round(12 * N / 1e6, 2), "render_ms": round(ms, 3),
+                                "fused_step_ms": round(step_ms, 3)})
+        plan.close()
+    out["paper_rtx3090_render_ms"] = {"dense": 4.02, "2:1": 2.58, "3:1": 2.33, "5:1": 2.13,
+                                      "7:1": 1.90, "10:1": 1.72}
+    return out
+
+
 # ------------------------------------------------------------------ 4K stress
 def stress_4k(dev, steps: int = 5, warmup: int = 2) -> dict:
     """2160 x 3840 RGB hologram, 1M Gaussians (scales 0.3-8 px), 6 planes z ~ U[0, 20] mm:
@@ -952,6 +1008,7 @@ def main():
             line["time_to_psnr_adan"] = time_to_psnr(dev, plan_tuning=tuned, optimizer="adan")
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
             line["stress_4k"] = stress_4k(dev)
+            line["render_sweep"] = render_sweep(dev)
             line["l_recon"] = recon_bench(dev, plan_tuning=tuned)
             line["poh_conversion"] = poh_bench(dev, plan_tuning=tuned)
         print(json.dumps(line), flush=True)
