@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   float2 v[I::GA::MB][I::A];
   reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
     const int y = y0 + b;
-    return y < H ? half[((size_t)(a / CB) * H + y) * CB + (a % CB)] : make_float2(0.f, 0.f);
+    return y < H ? __ldg(&half[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
   I::rest(v, u, buf, tw);
