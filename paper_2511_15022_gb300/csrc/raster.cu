@@ -198,12 +198,12 @@ __device__ __forceinline__ int stage_batch(const RasterConsts& rc, const float4*
                                            float4* srec, int* sgid) {
   const int i = base + threadIdx.x;
   if (i < count) {
-    int gid = exhaustive ? i : pairs[start + i];
+    int gid = exhaustive ? i : __ldg(&pairs[start + i]);
     const float4* g = rec + (size_t)gid * CGH_REC_F4;
 #pragma unroll
-    for (int k = 0; k < CGH_REC_F4; ++k) srec[threadIdx.x * CGH_REC_F4 + k] = g[k];
+    for (int k = 0; k < CGH_REC_F4; ++k) srec[threadIdx.x * CGH_REC_F4 + k] = __ldg(&g[k]);
     if (exhaustive) {
-      int4 r = rect[gid];
+      int4 r = __ldg(&rect[gid]);
       if (tx < r.x || tx > r.z || ty < r.y || ty > r.w)
         srec[threadIdx.x * CGH_REC_F4 + 2] = make_float4(1.f, 0.f, 1.f, 0.f);
     }
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float
   const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
   const float fpx = (float)px, fpy = (float)py;
   const float fox = (float)(tx * CGH_TILE), foy = (float)(ty * CGH_TILE);
-  const int start = tile_start[tile], end = tile_start[tile + 1];
+  const int start = __ldg(&tile_start[tile]), end = __ldg(&tile_start[tile + 1]);
   const bool exhaustive = (long long)end > rc.cap;
   const int count = exhaustive ? rc.N : end - start;
   float accr[C], acci[C];
@@ -324,8 +324,8 @@ struct ReduceScatter<1, OFF> {
 //   2C          SG  = sum G S (unclamped pairs), S = sum_c (A_c dRe_c + B_c dIm_c)
 //   2C+1..2C+5  sum u dx, u dy, u dx^2, u dx dy, u dy^2 with u = S alpha G (power unclamped)
 // One CTA per tile.  The tile's dL/dU is staged in shared memory; each warp takes one staged
-// Gaussian at a time and sweeps the pixels of its box inside the tile (8 x 4 or 16 x 2
-// lanes per step, by the box width), accumulating the moments in registers; one
+// Gaussian at a time and sweeps the pixels of its box inside the tile (flattened, one
+// pixel per lane per step), accumulating the moments in registers; one
 // reduce-scatter over the warp and NV global atomics per (Gaussian, tile) follow.  Pixels
 // outside the box fail the cutoff test anyway (the box bounds the cutoff ellipse with
 // margin), so the sum equals that over all pixels of the tile.
@@ -350,9 +350,9 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
     const bool inside = px < rc.W && py < rc.H;
     const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
 #pragma unroll
-    for (int c = 0; c < C; ++c) sdu[c][threadIdx.x] = inside ? dU[c * plane + o] : make_float2(0.f, 0.f);
+    for (int c = 0; c < C; ++c) sdu[c][threadIdx.x] = inside ? __ldg(&dU[c * plane + o]) : make_float2(0.f, 0.f);
   }
-  const int start = tile_start[tile], end = tile_start[tile + 1];
+  const int start = __ldg(&tile_start[tile]), end = __ldg(&tile_start[tile + 1]);
   const bool exhaustive = (long long)end > rc.cap;
   const int count = exhaustive ? rc.N : end - start;
   const float fox = (float)ox, foy = (float)oy;
@@ -375,16 +375,18 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
       const float4 r4 = srec[j * CGH_REC_F4 + 4];
       const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
       const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
-      const int lsh = (x1 - x0 >= 8) ? 4 : 3;  // lanes per row: 16 or 8
-      const int lx = lane & ((1 << lsh) - 1), ly = lane >> lsh, lrows = 32 >> lsh;
+      // the box's pixels, flattened: lane k takes pixels k, k + 32, ...; floor(k / bw) from
+      // one FP32 product, exact here because k < 256 and the fractional part of
+      // (k + 1/2) / bw stays at least 1/32 away from an integer
+      const int bw = x1 - x0 + 1, npx = bw * (y1 - y0 + 1);
+      const float inv_bw = 1.f / (float)bw;
       float acc[NVP];
 #pragma unroll
       for (int v = 0; v < NVP; ++v) acc[v] = 0.f;
-      for (int by = y0; by <= y1; by += lrows) {
-        const int ly_ = by + ly;
-        for (int bx = x0; bx <= x1; bx += (1 << lsh)) {
-          const int lx_ = bx + lx;
-          if (lx_ > x1 || ly_ > y1) continue;
+      for (int k = lane; k < npx; k += 32) {
+        const int ry = (int)(((float)k + 0.5f) * inv_bw);
+        const int lx_ = x0 + (k - ry * bw), ly_ = y0 + ry;
+        {
           const float dx = (float)(ox + lx_) - r0.x, dy = (float)(oy + ly_) - r0.y;
           const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
           if (p2 < r1.y) continue;
