@@ -917,15 +917,21 @@ def main():
 
     # ---- end to end through the public API with host buffers: pinned host target copied
     # in and the loss read back every step
+    # (double-buffered: step k + 1's target is copied on a side stream while step k runs)
+    from paper_2511_15022_gb300.pipeline import InputPipeline
     host_target = torch.from_numpy(target_np).pin_memory()
     host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
-    dev_target = torch.empty_like(target)
+    pipe = InputPipeline(tuple(target.shape), target.dtype, dev)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        dev_target.copy_(host_target, non_blocking=True)
+    pipe.put(host_target)
+    for k in range(args.steps):
+        dev_target = pipe.get()
+        if k + 1 < args.steps:
+            pipe.put(host_target)
         loss = step(dev_target)
+        pipe.release()
         host_loss.copy_(loss.detach().reshape(1), non_blocking=True)
     e1.record(stream)
     barrier()
