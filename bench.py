@@ -808,9 +808,10 @@ def main():
 
     args = ap.parse_args()
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2511_15022_gb300.replicas import (aggregate_throughput, max_over_ranks,
+                                                 rank_info, replica_seed)
+    ri = rank_info()
+    rank, world, local_rank = ri.rank, ri.world, ri.local_rank
 
     from paper_2511_15022_gb300 import inputs
     w = inputs.hd_1080p()
@@ -855,8 +856,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    params_np = inputs.params_for(w, seed=w.seed + rank)
-    target_np = inputs.blob_targets(w.L, w.C, w.H, w.W, seed=inputs.SEED_TARGETS + rank)
+    params_np = inputs.params_for(w, seed=replica_seed(w.seed, rank))
+    target_np = inputs.blob_targets(w.L, w.C, w.H, w.W, seed=replica_seed(inputs.SEED_TARGETS, rank))
     plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
                     max_gaussians=w.N, device=dev)
     params = {k: torch.from_numpy(v).to(dev).requires_grad_(True) for k, v in params_np.items()}
@@ -937,12 +938,9 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
-    t = torch.tensor([ms_total, e2e_ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total, e2e_ms = float(t[0]), float(t[1])
-    value = world * args.steps / (ms_total / 1000.0)
-    e2e_value = world * args.steps / (e2e_ms / 1000.0)
+    ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], device=dev)
+    value = aggregate_throughput(args.steps, world, ms_total)
+    e2e_value = aggregate_throughput(args.steps, world, e2e_ms)
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
