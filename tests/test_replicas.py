@@ -37,7 +37,7 @@ def _worker(rank, world, port, out):
 @pytest.mark.timeout(120)
 def test_two_gloo_ranks_share_the_max_time():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, join=True,
                            start_method="spawn")
