@@ -514,6 +514,92 @@ def render_sweep(dev, reps: int = 20) -> dict:
     return out
 
 
+# ------------------------------------------------------------------ resolution sweep
+def resolution_sweep(dev, reps: int = 5) -> dict:
+    """The paper's runtime comparison (Sec. 5.1: CUDA against the PyTorch development at
+    768x512, 1024x1024, 1920x1080, 2560x1440 with L = 3): this library's fused step against
+    the same step with the propagation written in PyTorch autograd + cuFFT (centred pad,
+    fft2, band-limited H, ifft2, crop, intensity MSE, backward) and this library's
+    rasteriser forward and backward, as in the paper's PyTorch path.  RGB, 8 um, planes at
+    0/5/10 mm, 0.0965 Gaussians per pixel.  Step time and peak device memory of each."""
+    import math
+
+    import torch
+
+    from paper_2511_15022_gb300 import cgh, inputs
+    rows = []
+    for H, W in ((512, 768), (1024, 1024), (1080, 1920), (1440, 2560)):
+        N = int(round(0.0965 * H * W))
+        w = inputs.custom(H, W, N, wavelengths_m=(638e-9, 520e-9, 450e-9), z_m=(0.0, 5e-3, 10e-3),
+                          seed=inputs.SEED_GAUSSIANS + 9)
+        C, L = w.C, w.L
+        p = {k: torch.from_numpy(v).to(dev) for k, v in inputs.params_for(w).items()}
+        t = torch.from_numpy(inputs.blob_targets(L, C, H, W)).to(dev)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        base = torch.cuda.memory_allocated(dev)
+        torch.cuda.reset_peak_memory_stats(dev)
+        plan = cgh.Plan(H, W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff, max_gaussians=N,
+                        device=dev)
+        g = plan.empty_grads(N)
+        loss = torch.empty(1, device=dev)
+        ours_ms = timed(lambda: plan.step(p, t, grads=g, loss_out=loss))
+        ours_gb = (torch.cuda.max_memory_allocated(dev) - base) / 1e9
+
+        Ny, Nx = 2 * H, 2 * W
+        oy, ox = (Ny - H) // 2, (Nx - W) // 2
+        fy = torch.fft.fftfreq(Ny, d=w.pitch_m, dtype=torch.float64, device=dev)
+        fx = torch.fft.fftfreq(Nx, d=w.pitch_m, dtype=torch.float64, device=dev)
+        torch.cuda.reset_peak_memory_stats(dev)
+        base2 = torch.cuda.memory_allocated(dev)
+        Hs = []
+        for d in w.z_m:
+            per_c = []
+            for lam in w.wavelengths_m:
+                fxm = 1.0 / (lam * math.sqrt((2 * d / (Nx * w.pitch_m)) ** 2 + 1))
+                fym = 1.0 / (lam * math.sqrt((2 * d / (Ny * w.pitch_m)) ** 2 + 1))
+                kz = 2 * math.pi * torch.sqrt(torch.clamp(1 / lam ** 2 - fx[None, :] ** 2 - fy[:, None] ** 2, min=0))
+                mask = (fx.abs()[None, :] < fxm) & (fy.abs()[:, None] < fym)
+                per_c.append(torch.where(mask, torch.exp(1j * kz * d), 0).to(torch.complex64))
+            Hs.append(torch.stack(per_c))
+        Hst = torch.stack(Hs)
+
+        def torch_step():
+            U0 = plan.raster_fwd(p).requires_grad_(True)
+            P = torch.nn.functional.pad(U0, (ox, Nx - W - ox, oy, Ny - H - oy))
+            Ud = torch.fft.ifft2(torch.fft.fft2(P)[None] * Hst)[..., oy:oy + H, ox:ox + W]
+            lo = ((Ud.abs() ** 2 - t) ** 2).mean()
+            lo.backward()
+            plan.raster_bwd(p, U0.grad.contiguous(), grads=g)
+
+        torch_ms = timed(torch_step)
+        torch_gb = (torch.cuda.max_memory_allocated(dev) - base2) / 1e9 + ours_gb
+        rows.append({"H": H, "W": W, "gaussians": N, "ours_ms": round(ours_ms, 3),
+                     "torch_cufft_ms": round(torch_ms, 3),
+                     "step_time_reduction": round(1 - ours_ms / torch_ms, 3),
+                     "ours_peak_gb": round(ours_gb, 3), "torch_cufft_peak_gb": round(torch_gb, 3)})
+        del Hst, Hs
+        plan.close()
+    return {"rows": rows,
+            "paper_rtx3090_step_time_reduction": {"768x512": 0.397, "1024x1024": 0.426,
+                                                  "1920x1080": 0.477, "2560x1440": 0.501},
+            "what": ("fused step of this library vs raster (this library) + PyTorch autograd / "
+                     "cuFFT propagation and loss; peak device memory of each (the PyTorch "
+                     "figure adds its propagation's peak to the shared plan)")}
+
+
 # ------------------------------------------------------------------ 4K stress
 def stress_4k(dev, steps: int = 5, warmup: int = 2) -> dict:
     """2160 x 3840 RGB hologram, 1M Gaussians (scales 0.3-8 px), 6 planes z ~ U[0, 20] mm:
@@ -1013,6 +1099,7 @@ def main():
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
             line["stress_4k"] = stress_4k(dev)
             line["render_sweep"] = render_sweep(dev)
+            line["resolution_sweep"] = resolution_sweep(dev)
             line["l_recon"] = recon_bench(dev, plan_tuning=tuned)
             line["poh_conversion"] = poh_bench(dev, plan_tuning=tuned)
         print(json.dumps(line), flush=True)
