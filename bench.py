@@ -177,8 +177,7 @@ class ClockSampler:
 
 
 FFT_SOURCES = ("fft.cuh", "fftreg.cuh", "blasm_common.cuh", "blasm_reg.cuh", "blasm_spec.h",
-               "blasm_spec_a.cu", "blasm_spec_b.cu", "blasm_spec_c.cu", "blasm.cu",
-               "cgh_internal.h")
+               "blasm_spec_*.cu", "blasm.cu", "cgh_internal.h")
 RASTER_SOURCES = ("raster.cu", "cgh_internal.h")
 
 
@@ -190,7 +189,7 @@ def kernel_source_sha(kernel: str = "") -> str:
     import hashlib
     csrc = os.path.join(ROOT, "paper_2511_15022_gb300", "csrc")
     if kernel.startswith(("k_rows_", "k_cols_")):
-        files = [os.path.join(csrc, f) for f in FFT_SOURCES]
+        files = [f for pat in FFT_SOURCES for f in glob.glob(os.path.join(csrc, pat))]
     elif kernel.startswith("k_raster_"):
         files = [os.path.join(csrc, f) for f in RASTER_SOURCES]
     else:

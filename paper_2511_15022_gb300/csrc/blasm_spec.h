@@ -30,16 +30,17 @@ bool spec_rows(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRow
 bool spec_cols(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
                cudaStream_t s, cudaError_t* err, bool dry);
 
-// per-translation-unit hooks, tried in order by spec_rows / spec_cols
-bool spec_rows_a(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRowArgs* a,
-                 cudaStream_t s, cudaError_t* err, bool dry);
-bool spec_cols_a(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
-                 cudaStream_t s, cudaError_t* err, bool dry);
-bool spec_rows_b(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRowArgs* a,
-                 cudaStream_t s, cudaError_t* err, bool dry);
-bool spec_cols_b(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
-                 cudaStream_t s, cudaError_t* err, bool dry);
-bool spec_rows_c(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRowArgs* a,
-                 cudaStream_t s, cudaError_t* err, bool dry);
-bool spec_cols_c(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
-                 cudaStream_t s, cudaError_t* err, bool dry);
+// per-translation-unit hooks (one file per group of padded lengths, compiled in
+// parallel), tried in order by spec_rows / spec_cols
+#define CGH_SPEC_HOOKS(X)                                                                      \
+  bool spec_rows_##X(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRowArgs* a, \
+                     cudaStream_t s, cudaError_t* err, bool dry);                             \
+  bool spec_cols_##X(int kind, int N, int CB, const cgh_plan* p, const float2* in,            \
+                     float2* out, cudaStream_t s, cudaError_t* err, bool dry);
+CGH_SPEC_HOOKS(a)
+CGH_SPEC_HOOKS(b)
+CGH_SPEC_HOOKS(c)
+CGH_SPEC_HOOKS(d)
+CGH_SPEC_HOOKS(e)
+CGH_SPEC_HOOKS(f)
+#undef CGH_SPEC_HOOKS

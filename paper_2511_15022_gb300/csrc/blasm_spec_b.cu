@@ -1,12 +1,11 @@
-// blasm_spec_b.cu -- specialised FFT passes for the smaller padded lengths of the batched
-// workload's size buckets (256x256 -> 512, 512 -> 1024, 640 -> 1280).
+// blasm_spec_b.cu -- specialised FFT passes for padded length 512 (256 x 256 images, the
+// smallest bucket of the batched workload).
 #include "blasm_reg.cuh"
 
 bool spec_rows_b(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const SpecRowArgs* a,
                  cudaStream_t s, cudaError_t* err, bool dry) {
   CGH_ROW_SPEC(512, 8, 8, 8, 4, 4, 256)
   CGH_ROW_SPEC(512, 8, 8, 8, 2, 2, 128)
-  CGH_ROW_SPEC(1024, 16, 8, 8, 2, 2, 256)
   return false;
 }
 
@@ -14,7 +13,5 @@ bool spec_cols_b(int kind, int N_, int CB_, const cgh_plan* p, const float2* in,
                  cudaStream_t s, cudaError_t* err, bool dry) {
   CGH_COL_SPEC(512, 8, 8, 8, 2, 128, 3)
   CGH_COL_SPEC(512, 8, 8, 8, 1, 64, 4)
-  CGH_COL_SPEC(1024, 16, 8, 8, 1, 128, 3)
-  CGH_COL_SPEC(1280, 16, 10, 8, 1, 160, 2)
   return false;
 }

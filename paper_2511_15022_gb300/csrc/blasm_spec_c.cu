@@ -1,21 +1,16 @@
 // blasm_spec_c.cu -- specialised FFT passes for padded lengths 1536 and 2048 (768- and
-// 1024-pixel image sides), the 2560x1440 hologram (padded 2880 x 5120) and the 2160x3840
-// one (padded 4320 x 7680).
+// 1024-pixel image sides).
 #include "blasm_reg.cuh"
 
 bool spec_rows_c(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const SpecRowArgs* a,
                  cudaStream_t s, cudaError_t* err, bool dry) {
   CGH_ROW_SPEC(1536, 16, 12, 8, 2, 2, 384)
   CGH_ROW_SPEC(2048, 16, 16, 8, 2, 2, 512)
-  CGH_ROW_SPEC(7680, 16, 20, 24, 1, 2, 480)
-  CGH_ROW_SPEC(5120, 16, 16, 20, 1, 2, 320)
   return false;
 }
 
 bool spec_cols_c(int kind, int N_, int CB_, const cgh_plan* p, const float2* in, float2* out,
                  cudaStream_t s, cudaError_t* err, bool dry) {
   CGH_COL_SPEC(2048, 16, 16, 8, 1, 256, 1)
-  CGH_COL_SPEC(4320, 24, 15, 12, 1, 384, 1)
-  CGH_COL_SPEC(2880, 12, 15, 16, 1, 240, 2)
   return false;
 }
