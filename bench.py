@@ -516,7 +516,8 @@ def render_sweep(dev, reps: int = 20) -> dict:
 # ------------------------------------------------------------------ resolution sweep
 def resolution_sweep(dev, reps: int = 5) -> dict:
     """The paper's runtime comparison (Sec. 5.1: CUDA against the PyTorch development at
-    768x512, 1024x1024, 1920x1080, 2560x1440 with L = 3): this library's fused step against
+    768x512, 1024x1024, 1920x1080, 2560x1440 with L = 3, and its largest, 3200x1800): this
+    library's fused step against
     the same step with the propagation written in PyTorch autograd + cuFFT (centred pad,
     fft2, band-limited H, ifft2, crop, intensity MSE, backward) and this library's
     rasteriser forward and backward, as in the paper's PyTorch path.  RGB, 8 um, planes at
@@ -527,7 +528,7 @@ def resolution_sweep(dev, reps: int = 5) -> dict:
 
     from paper_2511_15022_gb300 import cgh, inputs
     rows = []
-    for H, W in ((512, 768), (1024, 1024), (1080, 1920), (1440, 2560)):
+    for H, W in ((512, 768), (1024, 1024), (1080, 1920), (1440, 2560), (1800, 3200)):
         N = int(round(0.0965 * H * W))
         w = inputs.custom(H, W, N, wavelengths_m=(638e-9, 520e-9, 450e-9), z_m=(0.0, 5e-3, 10e-3),
                           seed=inputs.SEED_GAUSSIANS + 9)

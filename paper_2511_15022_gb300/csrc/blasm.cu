@@ -326,7 +326,8 @@ bool spec_rows(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRow
          spec_rows_c(kind, N, RB, CB, p, a, s, err, dry) ||
          spec_rows_d(kind, N, RB, CB, p, a, s, err, dry) ||
          spec_rows_e(kind, N, RB, CB, p, a, s, err, dry) ||
-         spec_rows_f(kind, N, RB, CB, p, a, s, err, dry);
+         spec_rows_f(kind, N, RB, CB, p, a, s, err, dry) ||
+         spec_rows_g(kind, N, RB, CB, p, a, s, err, dry);
 }
 
 bool spec_cols(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
@@ -336,7 +337,8 @@ bool spec_cols(int kind, int N, int CB, const cgh_plan* p, const float2* in, flo
          spec_cols_c(kind, N, CB, p, in, out, s, err, dry) ||
          spec_cols_d(kind, N, CB, p, in, out, s, err, dry) ||
          spec_cols_e(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_f(kind, N, CB, p, in, out, s, err, dry);
+         spec_cols_f(kind, N, CB, p, in, out, s, err, dry) ||
+         spec_cols_g(kind, N, CB, p, in, out, s, err, dry);
 }
 
 static bool try_spec_rows(int kind, cgh_plan* p, const SpecRowArgs& a, cudaStream_t s,

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   using F = typename P::F;
   using I = typename P::I;
   static_assert(I::C == F::A, "inverse must end where the forward starts");
+  static_assert(T % 32 == 0, "the loss reduction shuffles over whole warps");
   extern __shared__ float2 buf[];
   __shared__ float red[32];
   const int batch = blockIdx.y, y0 = blockIdx.x * NB;  // batch = l * C + c

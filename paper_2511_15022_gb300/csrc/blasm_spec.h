@@ -43,4 +43,5 @@ CGH_SPEC_HOOKS(c)
 CGH_SPEC_HOOKS(d)
 CGH_SPEC_HOOKS(e)
 CGH_SPEC_HOOKS(f)
+CGH_SPEC_HOOKS(g)
 #undef CGH_SPEC_HOOKS

@@ -1,7 +1,7 @@
 """Propagation parity for every specialised padded length: the batched workload's size
-buckets (512x768, 640x1024, 1024x1024 images), the 1440x2560 and 2160x3840 holograms, one
-channel and plane each against the oracle, plus specialised == generic kernels on the same
-plan."""
+buckets (512x768, 640x1024, 1024x1024 images), the 1440x2560, 1800x3200 and 2160x3840
+holograms, one channel and plane each against the oracle, plus specialised == generic
+kernels on the same plan."""
 import numpy as np
 import pytest
 
@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 FIELD_TOL = 1e-4
 
-SHAPES = [(512, 768), (640, 1024), (1024, 1024), (512, 512), (1440, 2560), (2160, 3840)]
+SHAPES = [(512, 768), (640, 1024), (1024, 1024), (512, 512), (1440, 2560), (1800, 3200),
+          (2160, 3840)]
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +42,7 @@ def test_blasm_matches_oracle(H, W, dev):
         assert rel_l2(dU0, refb) < FIELD_TOL
 
 
-@pytest.mark.parametrize("H,W", SHAPES[:5])
+@pytest.mark.parametrize("H,W", SHAPES[:6])
 def test_specialised_equals_generic(H, W, dev):
     import torch
     from paper_2511_15022_gb300 import cgh
