@@ -204,6 +204,19 @@ cgh_status cgh_forward_loss(cgh_plan* plan, const cgh_params* params, const floa
 cgh_status cgh_step(cgh_plan* plan, const cgh_params* params, const float* target,
                     float* loss_out, const cgh_grads* grads, void* stream);
 
+/* cgh_step as the backward pass of an autograd function (forward recomputed, Sec. 3.4):
+ *   grad_scale    device pointer to one float multiplying every gradient (the upstream
+ *                 gradient of the loss; NULL: 1), applied inside the gradient kernel;
+ *   reuse_binning nonzero: the caller guarantees that the parameter values are unchanged
+ *                 since the last call on this plan that rasterised them, so the
+ *                 per-Gaussian records and per-tile lists left in the workspace are reused
+ *                 instead of rebuilt.  If N or a parameter pointer differs from that call
+ *                 (or nothing was rasterised yet) they are rebuilt anyway.
+ * Everything else, including loss_out, as cgh_step. */
+cgh_status cgh_step_scaled(cgh_plan* plan, const cgh_params* params, const float* target,
+                           float* loss_out, const cgh_grads* grads, const float* grad_scale,
+                           int32_t reuse_binning, void* stream);
+
 /* One Adam step over up to 8 parameter groups in a single launch (PyTorch semantics, no
  * weight decay): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * p -= lr/(1-b1^t) * m / (sqrt(v)/sqrt(1-b2^t) + eps).  step >= 1.  The paper uses

@@ -2,9 +2,12 @@
 
 HologramLoss (Sec. 3.2 L_MSE through Algorithms 2 and 3): the forward runs raster ->
 BLASM -> loss and keeps only the parameters (no field, spectrum or intensity is
-stored); the backward recomputes the forward inside the fused cgh_step and returns the
-parameter gradients -- the recompute-instead-of-store trade of the paper's constant-VRAM
-backward.  With eager=True the forward already runs the fused step and keeps the
+stored); the backward recomputes the forward inside the fused step (cgh_step_scaled) and
+returns the parameter gradients -- the recompute-instead-of-store trade of the paper's
+constant-VRAM backward.  The upstream gradient is applied inside the library's gradient
+kernel, and the per-tile Gaussian lists the forward left in the plan's workspace are
+reused when no other call on the plan has rebinned since (the saved parameters cannot
+have changed: autograd rejects in-place changes to them).  With eager=True the forward already runs the fused step and keeps the
 O(N) parameter gradients instead (no recompute; still no per-pixel state).
 
 HologramIntensity returns I_l = |U(d_l)|^2 [L, C, H, W] for user-defined losses; its
@@ -34,19 +37,27 @@ class HologramLoss(torch.autograd.Function):
         else:
             loss = plan.forward_loss(p, target)
             ctx.save_for_backward(target, *[p[k] for k in PARAM_KEYS])
+            # the workspace now holds the binning of these parameters; autograd's version
+            # check guarantees their values are unchanged when backward runs, so backward
+            # may reuse it if no other call on the plan has rebinned in between
+            ctx.bin_generation = plan.bin_generation
         return loss.reshape(())
 
     @staticmethod
     def backward(ctx, grad_out):
         plan = ctx.plan
         if ctx.eager:
-            grads = list(ctx.saved_tensors)
+            # chain rule with the upstream scalar (1 for loss.backward())
+            grads = [g.mul_(grad_out) for g in ctx.saved_tensors]
         else:
             target, *ps = ctx.saved_tensors
-            _, g = plan.step(dict(zip(PARAM_KEYS, ps)), target)
+            reuse = plan.bin_generation == ctx.bin_generation
+            scale = grad_out.detach().reshape(1).to(torch.float32).contiguous()
+            # the recomputed forward and the backward in one call; the upstream scalar is
+            # applied inside the gradient kernel
+            _, g = plan.step(dict(zip(PARAM_KEYS, ps)), target, grad_scale=scale,
+                             reuse_binning=reuse)
             grads = [g[k] for k in PARAM_KEYS]
-        # chain rule with the upstream scalar (1 for loss.backward())
-        grads = [g.mul_(grad_out) for g in grads]
         return (None, None, None, *grads)
 
 

@@ -54,7 +54,7 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_plan_set_workspace", "cgh_plan_set_tuning", "cgh_plan_get_tuning",
            "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
-           "cgh_step", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
+           "cgh_step", "cgh_step_scaled", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
            "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
            "cgh_batch_destroy", "cgh_batch_bind", "cgh_batch_step", "cgh_batch_kernels_per_step",
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
     lib.cgh_intensity_loss.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.cgh_forward_loss.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp]
     lib.cgh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads), vp]
+    lib.cgh_step_scaled.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads),
+                                    vp, ctypes.c_int32, vp]
     lib.cgh_adam_step.argtypes = [ctypes.POINTER(_AdamGroup), i32, i32, f32, f32, f32, vp]
     lib.cgh_adam_step_table.argtypes = [vp, vp, i32, i64, i32, f32, f32, f32, f32, vp]
     lib.cgh_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
@@ -217,6 +219,9 @@ class Plan:
                                        self.pitch_m, zz, self.aperture, self.cutoff,
                                        self.max_gaussians, ctypes.byref(h)), "cgh_plan_create")
         self._h = h
+        # bumped by every call that may bin Gaussians into the workspace: a caller that saw
+        # the same value before and after its own calls knows the binning is still theirs
+        self.bin_generation = 0
         self._ws = None
         if tuning:
             self.set_tuning(**tuning)
@@ -333,6 +338,8 @@ class Plan:
                   "phase": (N, self.C), "alpha_raw": (N,)}
         for k in PARAM_KEYS:
             _need(p[k], torch.float32, shapes[k], k)
+        # every call that takes parameters may rebin them in the workspace
+        self.bin_generation += 1
         return _Params(N, *[ctypes.c_void_p(p[k].data_ptr()) for k in PARAM_KEYS])
 
     def empty_grads(self, N: int) -> Dict[str, torch.Tensor]:
@@ -424,17 +431,33 @@ class Plan:
                "cgh_autotune")
         return {k: getattr(best, k) for k, _ in _Tuning._fields_}
 
-    def step(self, params, target, grads=None, loss_out=None, stream=None):
-        """Fused forward + backward (cgh_step).  Returns (loss[1], grads)."""
+    def step(self, params, target, grads=None, loss_out=None, stream=None, grad_scale=None,
+             reuse_binning: bool = False):
+        """Fused forward + backward (cgh_step).  Returns (loss[1], grads).
+
+        grad_scale (a one-element float32 device tensor) multiplies every gradient and
+        reuse_binning keeps the workspace's binning of these parameters (cgh_step_scaled)."""
         prm = self._params(params)
         _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
         g = grads if grads is not None else self.empty_grads(prm.N)
         gs = self._grads(g, prm.N)
         loss = loss_out if loss_out is not None else torch.empty(1, dtype=torch.float32,
                                                                  device=self.device)
-        _check(_lib.cgh_step(self._h, ctypes.byref(prm), ctypes.c_void_p(target.data_ptr()),
-                             ctypes.c_void_p(loss.data_ptr()), ctypes.byref(gs),
-                             ctypes.c_void_p(_stream(stream))), "cgh_step")
+        if grad_scale is None and not reuse_binning:
+            _check(_lib.cgh_step(self._h, ctypes.byref(prm), ctypes.c_void_p(target.data_ptr()),
+                                 ctypes.c_void_p(loss.data_ptr()), ctypes.byref(gs),
+                                 ctypes.c_void_p(_stream(stream))), "cgh_step")
+            return loss, g
+        if grad_scale is not None:
+            if (grad_scale.dtype != torch.float32 or grad_scale.numel() != 1
+                    or grad_scale.device != self.device):
+                raise ValueError("grad_scale must be one float32 element on the plan's device")
+        _check(_lib.cgh_step_scaled(self._h, ctypes.byref(prm), ctypes.c_void_p(target.data_ptr()),
+                                    ctypes.c_void_p(loss.data_ptr()), ctypes.byref(gs),
+                                    ctypes.c_void_p(grad_scale.data_ptr() if grad_scale is not None
+                                                    else 0),
+                                    1 if reuse_binning else 0,
+                                    ctypes.c_void_p(_stream(stream))), "cgh_step_scaled")
         return loss, g
 
 

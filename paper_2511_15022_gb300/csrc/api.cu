@@ -269,6 +269,7 @@ extern "C" cgh_status cgh_plan_set_workspace(cgh_plan* plan, void* workspace, si
     return fail(CGH_ERR_WORKSPACE, "workspace of %zu bytes < required %zu", bytes, plan->ws_needed);
   plan->ws = (char*)workspace;
   plan->ws_bytes = bytes;
+  plan->bin_valid = 0;  // a new workspace holds no binning
   return CGH_OK;
 }
 
@@ -302,6 +303,7 @@ extern "C" cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* t) {
     plan->pair_cap_mult = t->pair_capacity_per_gaussian;
     const size_t before = plan->ws_needed;
     layout(plan);
+    plan->bin_valid = 0;  // the carve-up moved
     if (plan->ws && plan->ws_needed > plan->ws_bytes) {
       plan->ws = nullptr;
       plan->ws_bytes = 0;
@@ -439,12 +441,13 @@ extern "C" cgh_status cgh_intensity_loss(cgh_plan* plan, const void* Ud, const f
 }
 
 static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const float* target,
-                                float* loss_out, bool want_grad, cudaStream_t s) {
+                                float* loss_out, bool want_grad, cudaStream_t s,
+                                bool rebin = true) {
   float2* U0 = (float2*)(plan->ws + plan->off_U0);
   float2* Y = (float2*)(plan->ws + plan->off_Y);
   float2* V = (float2*)(plan->ws + plan->off_V);
   float* partials = (float*)(plan->ws + plan->off_loss);
-  CGH_TRY(launch_raster_fwd(plan, params, U0, s), "raster_fwd");
+  CGH_TRY(launch_raster_fwd(plan, params, U0, s, rebin), "raster_fwd");
   CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
   CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s), "cols_fwd_planes");
   CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad), "rows_loss");
@@ -459,21 +462,34 @@ extern "C" cgh_status cgh_forward_loss(cgh_plan* plan, const cgh_params* params,
   return forward_chain(plan, params, target, loss_out, false, (cudaStream_t)stream);
 }
 
-extern "C" cgh_status cgh_step(cgh_plan* plan, const cgh_params* params, const float* target,
-                               float* loss_out, const cgh_grads* grads, void* stream) {
+static cgh_status step_impl(cgh_plan* plan, const cgh_params* params, const float* target,
+                            float* loss_out, const cgh_grads* grads, const float* grad_scale,
+                            bool rebin, cudaStream_t s) {
   CGH_CHECK(check_call(plan, params));
   if (!params || !target || !loss_out) return fail(CGH_ERR_ARG, "NULL argument");
   CGH_CHECK(check_grads(params, grads));
-  cudaStream_t s = (cudaStream_t)stream;
-  CGH_CHECK(forward_chain(plan, params, target, loss_out, true, s));
+  CGH_CHECK(forward_chain(plan, params, target, loss_out, true, s, rebin));
   float2* U0 = (float2*)(plan->ws + plan->off_U0);  // reused for dL/dU(0)
   float2* Y = (float2*)(plan->ws + plan->off_Y);    // reused for the backward half grid
   float2* V = (float2*)(plan->ws + plan->off_V);
   CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s), "cols_bwd_planes");
   CGH_TRY(launch_rows_inv_crop(plan, Y, U0, plan->C, s), "rows_inv_crop");
   // the forward's binning is still valid for these parameters: reuse it
-  CGH_TRY(launch_raster_bwd(plan, params, U0, grads, s, false), "raster_bwd");
+  CGH_TRY(launch_raster_bwd(plan, params, U0, grads, s, false, grad_scale), "raster_bwd");
   return CGH_OK;
+}
+
+extern "C" cgh_status cgh_step(cgh_plan* plan, const cgh_params* params, const float* target,
+                               float* loss_out, const cgh_grads* grads, void* stream) {
+  return step_impl(plan, params, target, loss_out, grads, nullptr, true, (cudaStream_t)stream);
+}
+
+extern "C" cgh_status cgh_step_scaled(cgh_plan* plan, const cgh_params* params,
+                                      const float* target, float* loss_out,
+                                      const cgh_grads* grads, const float* grad_scale,
+                                      int32_t reuse_binning, void* stream) {
+  return step_impl(plan, params, target, loss_out, grads, grad_scale, reuse_binning == 0,
+                   (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ Adam

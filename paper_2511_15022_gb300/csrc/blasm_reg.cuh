@@ -97,6 +97,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // tstage = 1: the CTA's NB target rows are copied into shared memory (after the exchange
 // buffer) with asynchronous 16-byte copies issued before the inverse transform, so their
 // latency hides behind it (needs a 16-byte aligned target and W % 4 == 0).
@@ -273,6 +277,12 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
     const TFConst& tc = bl.tf[c * bl.L + l];
     const float4* src =
         reinterpret_cast<const float4*>(G + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB);
+    if (l + 1 < bl.L) {
+      // the next plane's slab (contiguous) into L2 while this one is transformed
+      const char* nxt = reinterpret_cast<const char*>(G + (size_t)((l + 1) * C + c) * H * Nx +
+                                                      (size_t)kb * H * CB);
+      for (int i = threadIdx.x; i * 128 < H * CB * 8; i += T) prefetch_l2(nxt + i * 128);
+    }
     float4 v[F::GA::MB][F::A];
     reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
       const int y = a - oy;

@@ -89,6 +89,9 @@ struct cgh_plan {
       off_pairs, off_status, off_loss, off_U0, off_Y, off_V, ws_needed;
   int64_t pair_capacity;
   int loss_slots;
+  // parameters the binning in the workspace was built for (bin_valid = 0: none)
+  int bin_valid;
+  cgh_params bin_params;
 };
 
 // status words in the workspace (int32 each)
@@ -104,11 +107,16 @@ LaunchShape fft_shape(const cgh_plan* p, const FFTDesc& d, int nb, int buffers);
 
 // ---- launch interfaces (return cudaError_t of the launch) ----
 // raster.cu
-cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s);
+// rebin = false reuses the binning in the workspace when it was built for these parameter
+// pointers and N (the caller vouches for the values); otherwise the Gaussians are binned.
+cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s,
+                              bool rebin = true);
 // rebin = false reuses the binning left in the workspace by the preceding raster_fwd with
 // the same parameters.
+// grad_scale: device float multiplying every gradient (NULL: 1).
 cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* dU,
-                              const cgh_grads* g, cudaStream_t s, bool rebin);
+                              const cgh_grads* g, cudaStream_t s, bool rebin,
+                              const float* grad_scale = nullptr);
 // blasm.cu
 cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,
                                 cudaStream_t s);

@@ -131,6 +131,9 @@ __global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__
 
 // Exclusive scan of tile counts (one CTA of 1024 threads).  tile_start has T+1 entries;
 // tile_count is reset to zero so that k_emit can use it as the per-tile cursor.
+// Each thread owns a contiguous chunk of `per` tiles; with per <= PER (a compile-time
+// bound) the chunk's counts are loaded once, all at the same time, into registers.
+template <int PER>
 __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
                                                      int* __restrict__ tile_count,
                                                      int* __restrict__ tile_start,
@@ -139,8 +142,16 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   const int tid = threadIdx.x, nt = blockDim.x;
   const int per = (T + nt - 1) / nt;
   const int beg = min(T, tid * per), end = min(T, beg + per);
+  int cnt[PER > 0 ? PER : 1];
   long long local = 0;
-  for (int i = beg; i < end; ++i) local += tile_count[i];
+  if constexpr (PER > 0) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) cnt[k] = (beg + k < end) ? tile_count[beg + k] : 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) local += cnt[k];
+  } else {
+    for (int i = beg; i < end; ++i) local += tile_count[i];
+  }
   // inclusive scan of `local` over the CTA
   long long v = local;
   const int lane = tid & 31, wid = tid >> 5;
@@ -160,11 +171,22 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   }
   __syncthreads();
   long long excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
-  for (int i = beg; i < end; ++i) {
-    int cnt = tile_count[i];
-    tile_start[i] = (int)min(excl, (long long)0x7fffffff);
-    excl += cnt;
-    tile_count[i] = 0;
+  if constexpr (PER > 0) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      if (beg + k < end) {
+        tile_start[beg + k] = (int)min(excl, (long long)0x7fffffff);
+        tile_count[beg + k] = 0;
+      }
+      excl += cnt[k];
+    }
+  } else {
+    for (int i = beg; i < end; ++i) {
+      int c = tile_count[i];
+      tile_start[i] = (int)min(excl, (long long)0x7fffffff);
+      excl += c;
+      tile_count[i] = 0;
+    }
   }
   if (tid == nt - 1) {
     tile_start[T] = (int)min(excl, (long long)0x7fffffff);
@@ -173,7 +195,6 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
     if (excl > cap) status[ST_OVERFLOW] = 1;
   }
 }
-
 __global__ void k_emit(RasterConsts rc, const int4* __restrict__ rect,
                        const int* __restrict__ tile_start, int* __restrict__ cursor,
                        int* __restrict__ pairs) {
@@ -426,10 +447,14 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
 
 template <int C>
 __global__ void k_grad_finalize(RasterConsts rc, cgh_params p, const float* __restrict__ raw,
-                                cgh_grads g) {
+                                cgh_grads g, const float* __restrict__ grad_scale) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= rc.N) return;
-  const float* r = raw + (size_t)n * CGH_RAW_STRIDE;
+  // every gradient is linear in the moments: the upstream scale is applied to them
+  const float sc = grad_scale ? *grad_scale : 1.f;
+  float r[2 * C + 6];
+#pragma unroll
+  for (int k = 0; k < 2 * C + 6; ++k) r[k] = sc * raw[(size_t)n * CGH_RAW_STRIDE + k];
   bool ok = finitef(p.xy_raw[2 * n]) && finitef(p.xy_raw[2 * n + 1]) &&
             finitef(p.s_raw[2 * n]) && finitef(p.s_raw[2 * n + 1]) && finitef(p.theta[n]) &&
             finitef(p.alpha_raw[n]);
@@ -507,6 +532,8 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, sizeof(int) * ST_COUNT, s);
   if (e != cudaSuccess) return e;
+  p->bin_valid = 1;
+  p->bin_params = *prm;
   const int nblk = (prm->N + 255) / 256;
   if (prm->N > 0) {
     prof_begin(KID_PREPROCESS, s);
@@ -515,7 +542,13 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
     prof_end(KID_PREPROCESS, s);
   }
   prof_begin(KID_SCAN_TILES, s);
-  k_scan_tiles<<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  const int per = (T + 1023) / 1024;
+  if (per <= 8)
+    k_scan_tiles<8><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  else if (per <= 32)
+    k_scan_tiles<32><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  else
+    k_scan_tiles<0><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
   prof_end(KID_SCAN_TILES, s);
   if (prm->N > 0) {
     prof_begin(KID_EMIT, s);
@@ -526,8 +559,16 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s) {
-  cudaError_t e = bin(p, prm, s);
+static bool same_params(const cgh_params* a, const cgh_params* b) {
+  return a->N == b->N && a->xy_raw == b->xy_raw && a->s_raw == b->s_raw &&
+         a->theta == b->theta && a->amp == b->amp && a->phase == b->phase &&
+         a->alpha_raw == b->alpha_raw;
+}
+
+cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s,
+                              bool rebin) {
+  const bool reuse = !rebin && p->bin_valid && same_params(&p->bin_params, prm);
+  cudaError_t e = reuse ? cudaSuccess : bin(p, prm, s);
   if (e != cudaSuccess) return e;
   RasterConsts rc = make_consts(p, prm->N);
   dim3 grid(p->tiles_x, p->tiles_y);
@@ -547,7 +588,8 @@ cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cud
 }
 
 cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* dU,
-                              const cgh_grads* g, cudaStream_t s, bool rebin) {
+                              const cgh_grads* g, cudaStream_t s, bool rebin,
+                              const float* grad_scale) {
   cudaError_t e = rebin ? bin(p, prm, s) : cudaSuccess;
   if (e != cudaSuccess) return e;
   float* raw = (float*)(p->ws + p->off_raw);
@@ -573,10 +615,10 @@ cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* 
   if (prm->N > 0) {
     prof_begin(KID_GRAD_FINALIZE, s);
     switch (p->C) {
-      case 1: k_grad_finalize<1><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
-      case 2: k_grad_finalize<2><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
-      case 3: k_grad_finalize<3><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
-      default: k_grad_finalize<4><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g); break;
+      case 1: k_grad_finalize<1><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g, grad_scale); break;
+      case 2: k_grad_finalize<2><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g, grad_scale); break;
+      case 3: k_grad_finalize<3><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g, grad_scale); break;
+      default: k_grad_finalize<4><<<nblk, 256, 0, s>>>(rc, *prm, raw, *g, grad_scale); break;
     }
     prof_end(KID_GRAD_FINALIZE, s);
   }
