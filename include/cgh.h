@@ -382,8 +382,8 @@ cgh_status cgh_poh_step(cgh_plan* plan, const cgh_params* params, const float* p
  * These are the denominators of the arithmetic rooflines the benchmark reports. */
 cgh_status cgh_measure_peaks(double* fp32_flops_per_s, double* sfu_ops_per_s, void* stream);
 
-/* Number of kernels launched by this thread's calls into the library so far (host
- * counter; used to report launches per step). */
+/* Number of kernels launched by the library in this process so far, from every thread
+ * (host counter; used to report launches per step). */
 int64_t cgh_launch_count(void);
 
 /* Per-kernel timing with CUDA events recorded on each kernel's own launch stream.

@@ -8,15 +8,17 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "blasm_spec.h"
 #include "cgh_internal.h"
 
 static thread_local char g_err[512] = "";
-static thread_local long long g_launches = 0;
+// process-wide: autograd runs backward passes on its own thread, and their launches count
+static std::atomic<long long> g_launches{0};
 
-void cgh_count_launch(int n) { g_launches += n; }
+void cgh_count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static cgh_status fail(cgh_status st, const char* fmt, ...) {
   va_list ap;
@@ -267,6 +269,10 @@ extern "C" cgh_status cgh_plan_set_workspace(cgh_plan* plan, void* workspace, si
   if (((uintptr_t)workspace) % 256 != 0) return fail(CGH_ERR_ARG, "workspace must be 256-byte aligned");
   if (bytes < plan->ws_needed)
     return fail(CGH_ERR_WORKSPACE, "workspace of %zu bytes < required %zu", bytes, plan->ws_needed);
+  // status words start at zero (the loss pass's CTA ticket relies on it)
+  cudaError_t e = cudaMemset((char*)workspace + plan->off_status, 0, sizeof(int) * ST_COUNT);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(CGH_ERR_CUDA, "%s", cudaGetErrorString(e));
   plan->ws = (char*)workspace;
   plan->ws_bytes = bytes;
   plan->bin_valid = 0;  // a new workspace holds no binning
@@ -308,6 +314,10 @@ extern "C" cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* t) {
       plan->ws = nullptr;
       plan->ws_bytes = 0;
       (void)before;
+    } else if (plan->ws) {
+      cudaError_t e = cudaMemset(plan->ws + plan->off_status, 0, sizeof(int) * ST_COUNT);
+      if (e == cudaSuccess) e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return fail(CGH_ERR_CUDA, "%s", cudaGetErrorString(e));
     }
   }
   return CGH_OK;
@@ -450,8 +460,7 @@ static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const 
   CGH_TRY(launch_raster_fwd(plan, params, U0, s, rebin), "raster_fwd");
   CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
   CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s), "cols_fwd_planes");
-  CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad), "rows_loss");
-  CGH_TRY(launch_loss_finalize(plan, partials, rows_loss_blocks(plan), loss_out, s), "loss_finalize");
+  CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad, loss_out), "rows_loss");
   return CGH_OK;
 }
 
@@ -504,6 +513,38 @@ struct AdamArgs {
   int n;
 };
 
+__device__ __forceinline__ float adam_one(float& p, float g, float& m, float& v, float b1,
+                                          float b2, float eps, float inv_sqrt_bc2, float step) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  p -= step * m / (sqrtf(v) * inv_sqrt_bc2 + eps);
+  return p;
+}
+
+// Four consecutive elements per thread and 16-byte accesses (every group 16-byte aligned
+// with a length divisible by 4; offsets a.off in units of 4 elements).
+__global__ void k_adam4(AdamArgs a, float b1, float b2, float eps, float inv_sqrt_bc2) {
+  const long long total = a.off[a.n];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int gi = 0;
+    while (i >= a.off[gi + 1]) ++gi;
+    const long long j = i - a.off[gi];
+    float4 p = reinterpret_cast<float4*>(a.p[gi])[j];
+    const float4 g = reinterpret_cast<const float4*>(a.g[gi])[j];
+    float4 m = reinterpret_cast<float4*>(a.m[gi])[j];
+    float4 v = reinterpret_cast<float4*>(a.v[gi])[j];
+    const float st = a.step_size[gi];
+    adam_one(p.x, g.x, m.x, v.x, b1, b2, eps, inv_sqrt_bc2, st);
+    adam_one(p.y, g.y, m.y, v.y, b1, b2, eps, inv_sqrt_bc2, st);
+    adam_one(p.z, g.z, m.z, v.z, b1, b2, eps, inv_sqrt_bc2, st);
+    adam_one(p.w, g.w, m.w, v.w, b1, b2, eps, inv_sqrt_bc2, st);
+    reinterpret_cast<float4*>(a.p[gi])[j] = p;
+    reinterpret_cast<float4*>(a.m[gi])[j] = m;
+    reinterpret_cast<float4*>(a.v[gi])[j] = v;
+  }
+}
+
 __global__ void k_adam(AdamArgs a, float b1, float b2, float eps, float inv_sqrt_bc2) {
   const long long total = a.off[a.n];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -539,12 +580,25 @@ cudaError_t launch_adam(const cgh_adam_group* groups, int n, int step, float b1,
     a.step_size[i] = (float)((double)groups[i].lr / bc1);
   }
   for (int i = n + 1; i < 9; ++i) a.off[i] = a.off[n];
-  const long long total = a.off[n];
+  long long total = a.off[n];
   if (total == 0) return cudaSuccess;
+  bool vec = true;
+  for (int i = 0; i < n; ++i) {
+    const uintptr_t bits = (uintptr_t)groups[i].param | (uintptr_t)groups[i].grad |
+                           (uintptr_t)groups[i].exp_avg | (uintptr_t)groups[i].exp_avg_sq;
+    vec = vec && (bits & 15u) == 0 && groups[i].count % 4 == 0;
+  }
+  if (vec) {
+    for (int i = 0; i <= 8; ++i) a.off[i] /= 4;
+    total /= 4;
+  }
   long long blocks = (total + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   prof_begin(KID_ADAM, s);
-  k_adam<<<(unsigned)blocks, 256, 0, s>>>(a, b1, b2, eps, (float)(1.0 / sqrt(bc2)));
+  if (vec)
+    k_adam4<<<(unsigned)blocks, 256, 0, s>>>(a, b1, b2, eps, (float)(1.0 / sqrt(bc2)));
+  else
+    k_adam<<<(unsigned)blocks, 256, 0, s>>>(a, b1, b2, eps, (float)(1.0 / sqrt(bc2)));
   prof_end(KID_ADAM, s);
   return cudaGetLastError();
 }
@@ -645,6 +699,6 @@ extern "C" cgh_status cgh_adan_step(const cgh_adan_group* groups, int32_t num_gr
   return CGH_OK;
 }
 
-extern "C" int64_t cgh_launch_count(void) { return g_launches; }
+extern "C" int64_t cgh_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 extern "C" const char* cgh_last_error_string(void) { return g_err; }

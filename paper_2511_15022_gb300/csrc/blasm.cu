@@ -358,7 +358,7 @@ cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int
                                 cudaStream_t s) {
   {
     cudaError_t e;
-    SpecRowArgs a{in, half, nullptr, nullptr, batches, 0};
+    SpecRowArgs a{in, half, nullptr, nullptr, batches, 0, nullptr, nullptr, 0.0};
     if (try_spec_rows(SPEC_ROWS_PAD_FWD, p, a, s, &e)) return e;
   }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
@@ -404,10 +404,12 @@ cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, i
 }
 
 cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
-                             cudaStream_t s, bool want_grad) {
+                             cudaStream_t s, bool want_grad, float* loss_out) {
+  const double inv = 1.0 / ((double)p->L * p->C * p->H * p->W);
   {
     cudaError_t e;
-    SpecRowArgs a{nullptr, V, target, partials, p->L * p->C, want_grad ? 1 : 0};
+    SpecRowArgs a{nullptr, V, target, partials, p->L * p->C, want_grad ? 1 : 0, loss_out,
+                  (int*)(p->ws + p->off_status) + ST_LOSS_TICKET, inv};
     if (try_spec_rows(SPEC_ROWS_LOSS, p, a, s, &e)) return e;
   }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
@@ -417,7 +419,9 @@ cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float*
   const size_t smem = sizeof(float2) * (size_t)bs * RB;
   CGH_DISPATCH_MAXB(KID_ROWS_LOSS, sh.maxb, k_rows_loss, grid, sh.threads, smem, s, p->bl, p->fx, RB, CB, bs,
                     V, target, partials, want_grad ? 1 : 0);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_loss_finalize(p, partials, rows_loss_blocks(p), loss_out, s);
 }
 
 cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s) {

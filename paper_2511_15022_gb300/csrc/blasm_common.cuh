@@ -153,4 +153,33 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return t;  // valid in thread 0
 }
 
+// Loss finalisation by the last CTA of a pass: each CTA has written its partial (thread 0)
+// before calling; the CTA that draws the last ticket sums all `count` partials in FP64 in
+// index order (the result does not depend on which CTA is last), writes sum * inv_norm to
+// out[0] and resets the ticket for the next launch.
+__device__ __forceinline__ void finalize_if_last(const float* partials, int count,
+                                                 double inv_norm, float* out, int* ticket) {
+  __shared__ int s_last;
+  __shared__ double s_red[32];
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's partial is visible before its ticket is
+    s_last = atomicAdd(ticket, 1) == count - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) acc += (double)__ldcg(&partials[i]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s_red[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+    out[0] = (float)(t * inv_norm);
+    *ticket = 0;
+  }
+}
+
 }  // namespace cgh

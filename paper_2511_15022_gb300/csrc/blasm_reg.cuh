@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
                                                   float2* __restrict__ V,
                                                   const float* __restrict__ target,
                                                   float* __restrict__ partials, int want_grad,
-                                                  int tstage) {
+                                                  int tstage, float* __restrict__ loss_out,
+                                                  int* __restrict__ ticket, double inv_norm) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using F = typename P::F;
   using I = typename P::I;
@@ -159,14 +160,17 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   });
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
-  if (!want_grad) return;
-  reg::first_in_regs<N, F::A, NB, T, false>(u);
-  float2 w[F::GC::MB][F::C];
-  F::rest(u, w, buf, tw);
-  reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
-    const int y = y0 + b;
-    if (y < H) half[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
-  });
+  if (want_grad) {
+    reg::first_in_regs<N, F::A, NB, T, false>(u);
+    float2 w[F::GC::MB][F::C];
+    F::rest(u, w, buf, tw);
+    reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
+      const int y = y0 + b;
+      if (y < H) half[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
+    });
+  }
+  // at the end, where no transform state is live
+  if (loss_out) finalize_if_last(partials, gridDim.x * gridDim.y, inv_norm, loss_out, ticket);
 }
 
 // Column kernels work on float4 elements: columns 2 s and 2 s + 1 of the CTA's column block
@@ -370,7 +374,8 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_LOSS, s);
-      k<<<grid, T, smem, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad, tstage);
+      k<<<grid, T, smem, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad, tstage,
+                              a->loss_out, a->ticket, a->inv_norm);
       prof_end(KID_ROWS_LOSS, s);
       break;
     }

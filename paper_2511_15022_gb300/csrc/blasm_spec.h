@@ -19,6 +19,9 @@ struct SpecRowArgs {
   float* partials;      // rows_loss
   int batches;
   int want_grad;
+  float* loss_out;      // rows_loss: the finished loss (sum of partials * inv_norm)
+  int* ticket;          // rows_loss: CTA counter, 0 on entry and on exit
+  double inv_norm;      // rows_loss
 };
 
 // Launch (dry = false) or only look up (dry = true) a specialised row kernel for transform

@@ -95,7 +95,10 @@ struct cgh_plan {
 };
 
 // status words in the workspace (int32 each)
-enum { ST_PAIRS_LO = 0, ST_PAIRS_HI = 1, ST_OVERFLOW = 2, ST_NONFINITE = 3, ST_COUNT = 8 };
+// ST_LOSS_TICKET: CTAs of the loss pass that have written their partial (the last one sums
+// them all and resets it to 0)
+enum { ST_PAIRS_LO = 0, ST_PAIRS_HI = 1, ST_OVERFLOW = 2, ST_NONFINITE = 3, ST_LOSS_TICKET = 4,
+       ST_COUNT = 8 };
 
 struct LaunchShape {
   int threads, maxb;
@@ -123,8 +126,11 @@ cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int
 cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s);
 cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, int batches,
                                  cudaStream_t s);
+// ... and the loss itself: loss_out[0] = sum(partials) / (L C H W), summed in FP64 in a
+// fixed order (by the pass's last CTA when a specialised kernel runs, else by
+// k_loss_finalize).
 cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
-                             cudaStream_t s, bool want_grad);
+                             cudaStream_t s, bool want_grad, float* loss_out);
 cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s);
 cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* target,
                                   float* partials, float2* dUd, cudaStream_t s);

@@ -46,22 +46,57 @@ struct RasterConsts {
 
 __device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
 
+// Pre-activation parameters of one Gaussian, loaded together up front (the loads are all
+// independent, so they are in flight at the same time).
+template <int C>
+struct RawParams {
+  float x, y, sx, sy, th, al, amp[C], ph[C];
+};
+
+template <int C>
+__device__ __forceinline__ RawParams<C> load_params(const cgh_params& p, int n) {
+  RawParams<C> r;
+  r.x = __ldg(&p.xy_raw[2 * n + 0]);
+  r.y = __ldg(&p.xy_raw[2 * n + 1]);
+  r.sx = __ldg(&p.s_raw[2 * n + 0]);
+  r.sy = __ldg(&p.s_raw[2 * n + 1]);
+  r.th = __ldg(&p.theta[n]);
+  r.al = __ldg(&p.alpha_raw[n]);
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    r.amp[c] = __ldg(&p.amp[n * C + c]);
+    r.ph[c] = __ldg(&p.phase[n * C + c]);
+  }
+  return r;
+}
+
+// every parameter finite (no short-circuit: nothing waits on one load to decide another)
+template <int C>
+__device__ __forceinline__ bool all_finite(const RawParams<C>& r) {
+  bool ok = finitef(r.x) & finitef(r.y) & finitef(r.sx) & finitef(r.sy) & finitef(r.th) &
+            finitef(r.al);
+#pragma unroll
+  for (int c = 0; c < C; ++c) ok = ok & finitef(r.amp[c]) & finitef(r.ph[c]);
+  return ok;
+}
+
 // Activated quantities of one Gaussian (shared by preprocess and finalize).
 struct Act {
   float tx, ty, mx, my, esx, esy, sx, sy, c, s, S00, S01, S11, det, i00, i01, i11, alpha;
 };
 
-__device__ __forceinline__ Act activate(const cgh_params& p, int n, int W, int H) {
+template <int C>
+__device__ __forceinline__ Act activate(const RawParams<C>& r, int W, int H) {
   Act a;
-  a.tx = tanhf(p.xy_raw[2 * n + 0]);
-  a.ty = tanhf(p.xy_raw[2 * n + 1]);
+  a.tx = tanhf(r.x);
+  a.ty = tanhf(r.y);
   a.mx = (a.tx + 1.0f) * 0.5f * (float)W;
   a.my = (a.ty + 1.0f) * 0.5f * (float)H;
-  a.esx = expf(p.s_raw[2 * n + 0]);
-  a.esy = expf(p.s_raw[2 * n + 1]);
+  a.esx = expf(r.sx);
+  a.esy = expf(r.sy);
   a.sx = a.esx + 0.1f;
   a.sy = a.esy + 0.1f;
-  sincosf(p.theta[n], &a.s, &a.c);
+  sincosf(r.th, &a.s, &a.c);
   float sx2 = a.sx * a.sx, sy2 = a.sy * a.sy;
   a.S00 = sx2 * a.c * a.c + sy2 * a.s * a.s + 0.1f;
   a.S01 = (sx2 - sy2) * a.c * a.s;
@@ -71,30 +106,28 @@ __device__ __forceinline__ Act activate(const cgh_params& p, int n, int W, int H
   a.i00 = a.S11 / ds;
   a.i01 = -a.S01 / ds;
   a.i11 = a.S00 / ds;
-  a.alpha = 1.0f / (1.0f + expf(-p.alpha_raw[n]));
+  a.alpha = 1.0f / (1.0f + expf(-r.al));
   return a;
 }
 
+template <int C>
 __global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__ rec,
                              int4* __restrict__ rect, int* __restrict__ tile_count,
                              int* __restrict__ status) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= rc.N) return;
-  const int C = rc.C;
-  bool ok = finitef(p.xy_raw[2 * n]) && finitef(p.xy_raw[2 * n + 1]) &&
-            finitef(p.s_raw[2 * n]) && finitef(p.s_raw[2 * n + 1]) && finitef(p.theta[n]) &&
-            finitef(p.alpha_raw[n]);
+  const RawParams<C> q = load_params<C>(p, n);
+  const bool ok = all_finite(q);
   float A[CGH_MAX_C] = {0.f, 0.f, 0.f, 0.f}, B[CGH_MAX_C] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
   for (int c = 0; c < C; ++c) {
-    float amp = p.amp[n * C + c], ph = p.phase[n * C + c];
-    ok = ok && finitef(amp) && finitef(ph);
     float sp, cp;
-    sincosf(ph, &sp, &cp);
-    A[c] = amp * cp;
-    B[c] = amp * sp;
+    sincosf(q.ph[c], &sp, &cp);
+    A[c] = q.amp[c] * cp;
+    B[c] = q.amp[c] * sp;
   }
   if (!ok) atomicExch(&status[ST_NONFINITE], 1);
-  Act a = activate(p, n, rc.W, rc.H);
+  Act a = activate(q, rc.W, rc.H);
   const float k = -0.5f * kLog2e;
   float thr = rc.cutoff > 0.f ? log2f(rc.cutoff / a.alpha) : -INFINITY;
   // box of the ellipse m <= m*, m* = 2 ln(alpha / cutoff) (power floor m = 100 in smooth
@@ -131,27 +164,30 @@ __global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__
 
 // Exclusive scan of tile counts (one CTA of 1024 threads).  tile_start has T+1 entries;
 // tile_count is reset to zero so that k_emit can use it as the per-tile cursor.
-// Each thread owns a contiguous chunk of `per` tiles; with per <= PER (a compile-time
-// bound) the chunk's counts are loaded once, all at the same time, into registers.
-template <int PER>
+// Each thread owns a contiguous chunk of `per` tiles.  STAGED: the counts pass through
+// shared memory (dynamic, scan_stage_ints(T) ints), so that global memory is read and
+// written with coalesced accesses -- with one CTA doing the whole scan, the chunked global
+// accesses would otherwise cost one L1 wavefront per thread per element.  The stage holds
+// element i at i + i / 32, which spreads a warp's chunk-wise accesses over all 32 banks.
+__host__ __device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ size_t scan_stage_ints(int T) { return (size_t)scan_pad(T) + 1; }
+
+template <bool STAGED>
 __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
                                                      int* __restrict__ tile_count,
                                                      int* __restrict__ tile_start,
                                                      int* __restrict__ status) {
+  extern __shared__ int stage[];
   __shared__ long long warp_sums[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int per = (T + nt - 1) / nt;
   const int beg = min(T, tid * per), end = min(T, beg + per);
-  int cnt[PER > 0 ? PER : 1];
-  long long local = 0;
-  if constexpr (PER > 0) {
-#pragma unroll
-    for (int k = 0; k < PER; ++k) cnt[k] = (beg + k < end) ? tile_count[beg + k] : 0;
-#pragma unroll
-    for (int k = 0; k < PER; ++k) local += cnt[k];
-  } else {
-    for (int i = beg; i < end; ++i) local += tile_count[i];
+  if (STAGED) {
+    for (int i = tid; i < T; i += nt) stage[scan_pad(i)] = tile_count[i];
+    __syncthreads();
   }
+  long long local = 0;
+  for (int i = beg; i < end; ++i) local += STAGED ? stage[scan_pad(i)] : tile_count[i];
   // inclusive scan of `local` over the CTA
   long long v = local;
   const int lane = tid & 31, wid = tid >> 5;
@@ -171,22 +207,17 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   }
   __syncthreads();
   long long excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
-  if constexpr (PER > 0) {
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      if (beg + k < end) {
-        tile_start[beg + k] = (int)min(excl, (long long)0x7fffffff);
-        tile_count[beg + k] = 0;
-      }
-      excl += cnt[k];
-    }
-  } else {
-    for (int i = beg; i < end; ++i) {
-      int c = tile_count[i];
-      tile_start[i] = (int)min(excl, (long long)0x7fffffff);
-      excl += c;
+  // exclusive starts replace the counts (in the stage) or go straight to global memory
+  for (int i = beg; i < end; ++i) {
+    const int c = STAGED ? stage[scan_pad(i)] : tile_count[i];
+    const int st = (int)min(excl, (long long)0x7fffffff);
+    if (STAGED) {
+      stage[scan_pad(i)] = st;
+    } else {
+      tile_start[i] = st;
       tile_count[i] = 0;
     }
+    excl += c;
   }
   if (tid == nt - 1) {
     tile_start[T] = (int)min(excl, (long long)0x7fffffff);
@@ -194,19 +225,38 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
     status[ST_PAIRS_HI] = (int)(excl >> 32);
     if (excl > cap) status[ST_OVERFLOW] = 1;
   }
+  if (STAGED) {
+    __syncthreads();
+    for (int i = tid; i < T; i += nt) {
+      tile_start[i] = stage[scan_pad(i)];
+      tile_count[i] = 0;  // k_emit's per-tile cursor
+    }
+  }
 }
+// The (Gaussian, tile) slots of one Gaussian: its cursor increments are issued in groups
+// of up to 8 tiles before any result is used, so their round trips overlap.
 __global__ void k_emit(RasterConsts rc, const int4* __restrict__ rect,
                        const int* __restrict__ tile_start, int* __restrict__ cursor,
                        int* __restrict__ pairs) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= rc.N) return;
-  int4 r = rect[n];
-  for (int ty = r.y; ty <= r.w; ++ty)
-    for (int tx = r.x; tx <= r.z; ++tx) {
-      int t = ty * rc.tiles_x + tx;
-      long long pos = (long long)tile_start[t] + atomicAdd(&cursor[t], 1);
+  const int4 r = __ldg(&rect[n]);
+  const int bw = r.z - r.x + 1, cnt = (r.z >= r.x && r.w >= r.y) ? bw * (r.w - r.y + 1) : 0;
+  for (int k0 = 0; k0 < cnt; k0 += 8) {
+    int t[8], slot[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int kk = k0 + k;
+      t[k] = kk < cnt ? (r.y + kk / bw) * rc.tiles_x + r.x + kk % bw : -1;
+      slot[k] = t[k] >= 0 ? atomicAdd(&cursor[t[k]], 1) : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (t[k] < 0) continue;
+      const long long pos = (long long)__ldg(&tile_start[t[k]]) + slot[k];
       if (pos < rc.cap) pairs[pos] = n;
     }
+  }
 }
 
 // Stage records [base, base + 256) of a tile's list into shared memory.  In exhaustive
@@ -450,29 +500,27 @@ __global__ void k_grad_finalize(RasterConsts rc, cgh_params p, const float* __re
                                 cgh_grads g, const float* __restrict__ grad_scale) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= rc.N) return;
+  const RawParams<C> q = load_params<C>(p, n);
   // every gradient is linear in the moments: the upstream scale is applied to them
-  const float sc = grad_scale ? *grad_scale : 1.f;
+  const float sc = grad_scale ? __ldg(grad_scale) : 1.f;
   float r[2 * C + 6];
 #pragma unroll
-  for (int k = 0; k < 2 * C + 6; ++k) r[k] = sc * raw[(size_t)n * CGH_RAW_STRIDE + k];
-  bool ok = finitef(p.xy_raw[2 * n]) && finitef(p.xy_raw[2 * n + 1]) &&
-            finitef(p.s_raw[2 * n]) && finitef(p.s_raw[2 * n + 1]) && finitef(p.theta[n]) &&
-            finitef(p.alpha_raw[n]);
-  for (int c = 0; c < C; ++c) ok = ok && finitef(p.amp[n * C + c]) && finitef(p.phase[n * C + c]);
-  if (!ok) {
+  for (int k = 0; k < 2 * C + 6; ++k) r[k] = sc * __ldg(&raw[(size_t)n * CGH_RAW_STRIDE + k]);
+  if (!all_finite(q)) {
     g.xy_raw[2 * n] = 0.f; g.xy_raw[2 * n + 1] = 0.f; g.s_raw[2 * n] = 0.f;
     g.s_raw[2 * n + 1] = 0.f; g.theta[n] = 0.f; g.alpha_raw[n] = 0.f;
     for (int c = 0; c < C; ++c) { g.amp[n * C + c] = 0.f; g.phase[n * C + c] = 0.f; }
     return;
   }
-  Act a = activate(p, n, rc.W, rc.H);
+  Act a = activate(q, rc.W, rc.H);
   // items 1, 2: amplitude and phase
+#pragma unroll
   for (int c = 0; c < C; ++c) {
     float sp, cp;
-    sincosf(p.phase[n * C + c], &sp, &cp);
+    sincosf(q.ph[c], &sp, &cp);
     const float P = r[c], Q = r[C + c];
     g.amp[n * C + c] = cp * P + sp * Q;
-    g.phase[n * C + c] = p.amp[n * C + c] * (cp * Q - sp * P);
+    g.phase[n * C + c] = q.amp[c] * (cp * Q - sp * P);
   }
   // item 3: opacity through the sigmoid
   g.alpha_raw[n] = r[2 * C] * a.alpha * (1.f - a.alpha);
@@ -521,6 +569,9 @@ static RasterConsts make_consts(const cgh_plan* p, int N) {
   return rc;
 }
 
+// largest tile-count stage of k_scan_tiles (about 48K tiles: a 3072 x 4096 image at 16 x 16)
+constexpr size_t kScanStageBytes = 200 * 1024;
+
 // Binning shared by forward and backward: preprocess, scan, emit.
 static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   const int T = p->tiles_x * p->tiles_y;
@@ -537,18 +588,31 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   const int nblk = (prm->N + 255) / 256;
   if (prm->N > 0) {
     prof_begin(KID_PREPROCESS, s);
-    k_preprocess<<<nblk, 256, 0, s>>>(rc, *prm, (float4*)(p->ws + p->off_rec),
-                                      (int4*)(p->ws + p->off_rect), tile_count, status);
+    float4* rec = (float4*)(p->ws + p->off_rec);
+    int4* rect = (int4*)(p->ws + p->off_rect);
+    switch (p->C) {
+      case 1: k_preprocess<1><<<nblk, 256, 0, s>>>(rc, *prm, rec, rect, tile_count, status); break;
+      case 2: k_preprocess<2><<<nblk, 256, 0, s>>>(rc, *prm, rec, rect, tile_count, status); break;
+      case 3: k_preprocess<3><<<nblk, 256, 0, s>>>(rc, *prm, rec, rect, tile_count, status); break;
+      default: k_preprocess<4><<<nblk, 256, 0, s>>>(rc, *prm, rec, rect, tile_count, status); break;
+    }
     prof_end(KID_PREPROCESS, s);
   }
   prof_begin(KID_SCAN_TILES, s);
-  const int per = (T + 1023) / 1024;
-  if (per <= 8)
-    k_scan_tiles<8><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
-  else if (per <= 32)
-    k_scan_tiles<32><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
-  else
-    k_scan_tiles<0><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  const size_t stage_bytes = sizeof(int) * scan_stage_ints(T);
+  if (stage_bytes <= kScanStageBytes) {
+    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_scan_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kScanStageBytes);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_scan_tiles<true><<<1, 1024, stage_bytes, s>>>(T, p->pair_capacity, tile_count, tile_start,
+                                                    status);
+  } else {
+    k_scan_tiles<false><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  }
   prof_end(KID_SCAN_TILES, s);
   if (prm->N > 0) {
     prof_begin(KID_EMIT, s);
