@@ -98,7 +98,7 @@ static void layout(cgh_plan* p) {
   p->off_rec = o;        o = align256(o + N * CGH_REC_F4 * sizeof(float4));
   p->off_rect = o;       o = align256(o + N * sizeof(int4));
   p->off_raw = o;        o = align256(o + N * CGH_RAW_STRIDE * sizeof(float));
-  p->off_tile_count = o; o = align256(o + T * sizeof(int));
+  p->off_tile_count = o; o = align256(o + T * CGH_COUNT_STRIDE * sizeof(int));
   p->off_tile_start = o; o = align256(o + (T + 1) * sizeof(int));
   p->off_pairs = o;      o = align256(o + (size_t)p->pair_capacity * sizeof(int));
   p->off_status = o;     o = align256(o + ST_COUNT * sizeof(int));

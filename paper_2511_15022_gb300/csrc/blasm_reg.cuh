@@ -30,8 +30,15 @@ struct RegPlan {
   static constexpr int BUF = reg::BufSize<N, NB, R0, R1, R2>::elems;
   static constexpr size_t SMEM = sizeof(E) * (size_t)BUF;
   // exchange buffer + one thread-private slot per register of a last pass (column kernels)
-  static constexpr size_t SMEM_SLOTS =
-      SMEM + sizeof(E) * (size_t)F::GC::MB * F::C * T;
+  static constexpr size_t SLOTS = sizeof(E) * (size_t)F::GC::MB * F::C * T;
+  static constexpr size_t SMEM_SLOTS = SMEM + SLOTS;
+  // ... with a second, dense exchange buffer (two barriers per transform instead of four)
+  static constexpr int BUF2 = N * NB;
+  static constexpr size_t SMEM_SLOTS_DB = SMEM + sizeof(E) * (size_t)BUF2 + SLOTS;
+  // double-buffer when `resident` CTAs still fit in the SM's 228 KB (1 KB reserved per CTA)
+  static constexpr bool db_fits(int resident) {
+    return (size_t)resident * (SMEM_SLOTS_DB + 1024) <= (size_t)228 * 1024;
+  }
 };
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
@@ -213,7 +220,9 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
   using I = typename P::I;
   static_assert(F::C == I::A, "inverse must start where the forward ends");
   constexpr int CB = 2 * NB;
+  constexpr bool DB = P::db_fits(MINB);
   extern __shared__ float4 buf4[];
+  float4* by = buf4 + P::BUF;  // second exchange buffer (DB)
   const int c = blockIdx.y, kb = blockIdx.x;
   const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
   const float4* src = reinterpret_cast<const float4*>(Y + (size_t)c * H * Nx + (size_t)kb * H * CB);
@@ -224,10 +233,10 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
   });
   // the spectrum is parked in thread-private shared-memory slots (one 16-byte load per
   // element per plane) so that the inverse passes get the registers
-  float4* spec = buf4 + P::BUF;
+  float4* spec = buf4 + P::BUF + (DB ? P::BUF2 : 0);
   {
     float4 S[F::GC::MB][F::C];
-    F::rest(v, S, buf4, tw);
+    if constexpr (DB) F::rest2(v, S, buf4, by, tw); else F::rest(v, S, buf4, tw);
 #pragma unroll
     for (int i = 0; i < F::GC::MB; ++i)
 #pragma unroll
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
     }
     reg::first_in_regs<N, I::A, NB, T, true>(Z);
     float4 u[I::GC::MB][I::C];
-    I::rest(Z, u, buf4, tw);
+    if constexpr (DB) I::rest2(Z, u, buf4, by, tw); else I::rest(Z, u, buf4, tw);
     float4* dst = reinterpret_cast<float4*>(V + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB);
     reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float4& val) {
       const int y = a - oy;
@@ -272,11 +281,13 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
   using I = typename P::I;
   static_assert(F::C == I::A, "inverse must start where the forward ends");
   constexpr int CB = 2 * NB;
+  constexpr bool DB = P::db_fits(MINB);
   extern __shared__ float4 buf4[];
+  float4* by = buf4 + P::BUF;  // second exchange buffer (DB)
   const int c = blockIdx.y, kb = blockIdx.x;
   const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
   // the running sum over planes lives in thread-private shared-memory slots
-  float4* accs = buf4 + P::BUF;
+  float4* accs = buf4 + P::BUF + (DB ? P::BUF2 : 0);
   for (int l = 0; l < bl.L; ++l) {
     const TFConst& tc = bl.tf[c * bl.L + l];
     const float4* src =
@@ -293,7 +304,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
       return (y >= 0 && y < H) ? __ldg(&src[y * NB + b]) : make_float4(0.f, 0.f, 0.f, 0.f);
     });
     float4 S[F::GC::MB][F::C];
-    F::rest(v, S, buf4, tw);
+    if constexpr (DB) F::rest2(v, S, buf4, by, tw); else F::rest(v, S, buf4, tw);
 #pragma unroll
     for (int i = 0; i < F::GC::MB; ++i) {
       const int q = threadIdx.x + i * T;
@@ -319,7 +330,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
     for (int r = 0; r < I::A; ++r) acc[i][r] = cscale(accs[(i * I::A + r) * T + threadIdx.x], bl.inv_ntot);
   reg::first_in_regs<N, I::A, NB, T, true>(acc);
   float4 u[I::GC::MB][I::C];
-  I::rest(acc, u, buf4, tw);
+  if constexpr (DB) I::rest2(acc, u, buf4, by, tw); else I::rest(acc, u, buf4, tw);
   float4* dst = reinterpret_cast<float4*>(D + (size_t)c * H * Nx + (size_t)kb * H * CB);
   reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float4& val) {
     const int y = a - oy;
@@ -388,6 +399,7 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
                             cudaStream_t s) {
   using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
   static_assert(P::F::C == P::I::A, "slot layout shared by the forward end and inverse start");
+  constexpr size_t smem = P::db_fits(MINB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
   dim3 grid(p->bl.Nx / (2 * NB), p->C);
   const float2* tw = p->fy.tw;
   cudaError_t e = cudaSuccess;
@@ -397,18 +409,18 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
   if (kind == SPEC_COLS_FWD_PLANES) {
     auto k = all_in ? kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, true>
                     : kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
-    e = reg_set_smem(k, P::SMEM_SLOTS, MINB);
+    e = reg_set_smem(k, smem, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
-    k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);
+    k<<<grid, T, smem, s>>>(p->bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
     auto k = all_in ? kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, true>
                     : kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
-    e = reg_set_smem(k, P::SMEM_SLOTS, MINB);
+    e = reg_set_smem(k, smem, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
-    k<<<grid, T, P::SMEM_SLOTS, s>>>(p->bl, tw, in, out);
+    k<<<grid, T, smem, s>>>(p->bl, tw, in, out);
     prof_end(KID_COLS_BWD_PLANES, s);
   }
   return cudaGetLastError();

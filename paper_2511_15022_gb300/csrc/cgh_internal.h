@@ -15,6 +15,10 @@
 #define CGH_RAW_STRIDE 16
 // per-Gaussian render record: 5 float4 (see raster.cu)
 #define CGH_REC_F4 5
+// per-tile Gaussian counters (also the emit cursors) sit one per 32-byte sector: their
+// atomics then spread over many L2 lines instead of queueing on the few that a dense array
+// occupies
+#define CGH_COUNT_STRIDE 8
 // largest CTA of the FFT passes (their __launch_bounds__)
 constexpr int kMaxFFTThreads = 512;
 // opt-in dynamic shared memory per CTA on sm_103a (227 KB)

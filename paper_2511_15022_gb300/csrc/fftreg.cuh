@@ -208,6 +208,22 @@ struct Seq {
     __syncthreads();
     pass_from_smem<N, C, A * B, NB, T, INV, 0, E>(out, buf, tw);
   }
+
+  // Same with two exchange buffers (bx: first-pass layout, BufSize elements; by: dense, N NB
+  // elements) and two barriers instead of four.  A buffer is rewritten only by a thread that
+  // has passed a barrier which every reader of its previous contents reached after reading:
+  // bx was last read by the previous sequence's middle pass (before that sequence's second
+  // barrier), by by its last pass (before this sequence's first barrier).
+  __device__ __forceinline__ static void rest2(E (&in)[GA::MB][A], E (&out)[GC::MB][C], E* bx,
+                                               E* by, const float2* __restrict__ tw) {
+    pass_to_smem<N, A, 1, NB, T, A, E>(in, bx);
+    __syncthreads();
+    E mid[GB::MB][B];
+    pass_from_smem<N, B, A, NB, T, INV, A, E>(mid, bx, tw);
+    pass_to_smem<N, B, A, NB, T, 0, E>(mid, by);
+    __syncthreads();
+    pass_from_smem<N, C, A * B, NB, T, INV, 0, E>(out, by, tw);
+  }
 };
 
 }  // namespace reg

@@ -75,7 +75,7 @@ extern "C" cgh_status cgh_raster_fwd_noalloc(int32_t H, int32_t W, int32_t C, fl
   view.off_rec = o;        o = align256(o + N * CGH_REC_F4 * sizeof(float4));
   view.off_rect = o;       o = align256(o + N * sizeof(int4));
   view.off_raw = o;        // unused by the forward pass
-  view.off_tile_count = o; o = align256(o + T * sizeof(int));
+  view.off_tile_count = o; o = align256(o + T * CGH_COUNT_STRIDE * sizeof(int));
   view.off_tile_start = o; o = align256(o + (T + 1) * sizeof(int));
   view.off_status = o;     o = align256(o + ST_COUNT * sizeof(int));
   view.off_pairs = o;

@@ -159,7 +159,7 @@ __global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__
   o[4] = make_float4(A[2], B[2], A[3], B[3]);
   rect[n] = r;
   for (int ty = r.y; ty <= r.w; ++ty)
-    for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&tile_count[ty * rc.tiles_x + tx], 1);
+    for (int tx = r.x; tx <= r.z; ++tx) atomicAdd(&tile_count[(ty * rc.tiles_x + tx) * CGH_COUNT_STRIDE], 1);
 }
 
 // Exclusive scan of tile counts (one CTA of 1024 threads).  tile_start has T+1 entries;
@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   const int per = (T + nt - 1) / nt;
   const int beg = min(T, tid * per), end = min(T, beg + per);
   if (STAGED) {
-    for (int i = tid; i < T; i += nt) stage[scan_pad(i)] = tile_count[i];
+    for (int i = tid; i < T; i += nt) stage[scan_pad(i)] = tile_count[i * CGH_COUNT_STRIDE];
     __syncthreads();
   }
   long long local = 0;
-  for (int i = beg; i < end; ++i) local += STAGED ? stage[scan_pad(i)] : tile_count[i];
+  for (int i = beg; i < end; ++i) local += STAGED ? stage[scan_pad(i)] : tile_count[i * CGH_COUNT_STRIDE];
   // inclusive scan of `local` over the CTA
   long long v = local;
   const int lane = tid & 31, wid = tid >> 5;
@@ -209,13 +209,13 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   long long excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
   // exclusive starts replace the counts (in the stage) or go straight to global memory
   for (int i = beg; i < end; ++i) {
-    const int c = STAGED ? stage[scan_pad(i)] : tile_count[i];
+    const int c = STAGED ? stage[scan_pad(i)] : tile_count[i * CGH_COUNT_STRIDE];
     const int st = (int)min(excl, (long long)0x7fffffff);
     if (STAGED) {
       stage[scan_pad(i)] = st;
     } else {
       tile_start[i] = st;
-      tile_count[i] = 0;
+      tile_count[i * CGH_COUNT_STRIDE] = 0;
     }
     excl += c;
   }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
     __syncthreads();
     for (int i = tid; i < T; i += nt) {
       tile_start[i] = stage[scan_pad(i)];
-      tile_count[i] = 0;  // k_emit's per-tile cursor
+      tile_count[i * CGH_COUNT_STRIDE] = 0;  // k_emit's per-tile cursor
     }
   }
 }
@@ -248,7 +248,7 @@ __global__ void k_emit(RasterConsts rc, const int4* __restrict__ rect,
     for (int k = 0; k < 8; ++k) {
       const int kk = k0 + k;
       t[k] = kk < cnt ? (r.y + kk / bw) * rc.tiles_x + r.x + kk % bw : -1;
-      slot[k] = t[k] >= 0 ? atomicAdd(&cursor[t[k]], 1) : 0;
+      slot[k] = t[k] >= 0 ? atomicAdd(&cursor[t[k] * CGH_COUNT_STRIDE], 1) : 0;
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -579,7 +579,7 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   int* tile_count = (int*)(p->ws + p->off_tile_count);
   int* tile_start = (int*)(p->ws + p->off_tile_start);
   int* status = (int*)(p->ws + p->off_status);
-  cudaError_t e = cudaMemsetAsync(tile_count, 0, sizeof(int) * T, s);
+  cudaError_t e = cudaMemsetAsync(tile_count, 0, sizeof(int) * CGH_COUNT_STRIDE * (size_t)T, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, sizeof(int) * ST_COUNT, s);
   if (e != cudaSuccess) return e;
