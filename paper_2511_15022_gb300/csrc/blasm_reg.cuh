@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __gr
     return (x >= 0 && x < W && y < H) ? __ldg(&src[(size_t)y * W + x]) : make_float2(0.f, 0.f);
   });
   float2 out[F::GC::MB][F::C];
-  F::rest(v, out, buf, tw);
+  F::template rest<false>(v, out, buf, tw);  // first transform: no earlier reader
   float2* dst = half + (size_t)batch * H * N;
   reg::for_each<N, F::C, NB, T>(out, [&](int b, int a, float2& val) {
     const int y = y0 + b;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
     return y < H ? __ldg(&src[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
-  I::rest(v, u, buf, tw);
+  I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
   float2* dst = out + (size_t)batch * H * W;
   reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
     const int x = a - ox, y = y0 + b;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     return y < H ? __ldg(&half[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
-  I::rest(v, u, buf, tw);
+  I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
   if (tstage) {
     cp_async_wait_all();
     __syncthreads();
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   if (want_grad) {
     reg::first_in_regs<N, F::A, NB, T, false>(u);
     float2 w[F::GC::MB][F::C];
-    F::rest(u, w, buf, tw);
+    // block_sum's barriers follow the inverse transform's last reads of buf
+    F::template rest<false>(u, w, buf, tw);
     reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
       const int y = y0 + b;
       if (y < H) half[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;

@@ -196,9 +196,12 @@ struct Seq {
   using GB = Geo<N, B, NB, T>;
   using GC = Geo<N, C, NB, T>;
 
+  // FENCE = false: the caller guarantees that no thread still reads buf (first transform of
+  // the kernel, or a barrier since the previous sequence's last pass).
+  template <bool FENCE = true>
   __device__ __forceinline__ static void rest(E (&in)[GA::MB][A], E (&out)[GC::MB][C], E* buf,
                                               const float2* __restrict__ tw) {
-    __syncthreads();  // buf may still be read by a previous sequence's last pass
+    if (FENCE) __syncthreads();  // buf may still be read by a previous sequence's last pass
     pass_to_smem<N, A, 1, NB, T, A, E>(in, buf);
     __syncthreads();
     E mid[GB::MB][B];
