@@ -39,7 +39,16 @@ struct RegPlan {
   static constexpr bool db_fits(int resident) {
     return (size_t)resident * (SMEM_SLOTS_DB + 1024) <= (size_t)228 * 1024;
   }
+  // row kernels: exchange buffers (+ `extra` bytes of staging) without slots
+  static constexpr bool db_rows_fits(int resident, size_t extra) {
+    return (size_t)resident * (SMEM + sizeof(E) * (size_t)BUF2 + extra + 1024) <=
+           (size_t)228 * 1024;
+  }
 };
+
+// largest target stage of kr_rows_loss (NB rows of W = N / 2 floats)
+template <int N, int NB>
+constexpr size_t rows_stage_bytes() { return sizeof(float) * (size_t)NB * (N / 2); }
 
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
@@ -48,6 +57,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __gr
                                                      float2* __restrict__ half) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using F = typename P::F;
+  constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), 0);
   extern __shared__ float2 buf[];
   const int batch = blockIdx.y, y0 = blockIdx.x * NB;
   const int H = bl.H, W = bl.W, ox = bl.ox;
@@ -58,7 +68,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __gr
     return (x >= 0 && x < W && y < H) ? __ldg(&src[(size_t)y * W + x]) : make_float2(0.f, 0.f);
   });
   float2 out[F::GC::MB][F::C];
-  F::template rest<false>(v, out, buf, tw);  // first transform: no earlier reader
+  if constexpr (DB) F::rest2(v, out, buf, buf + P::BUF, tw);
+  else F::template rest<false>(v, out, buf, tw);  // first transform: no earlier reader
   float2* dst = half + (size_t)batch * H * N;
   reg::for_each<N, F::C, NB, T>(out, [&](int b, int a, float2& val) {
     const int y = y0 + b;
@@ -73,6 +84,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
                                                       float2* __restrict__ out) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using I = typename P::I;
+  constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), 0);
   extern __shared__ float2 buf[];
   const int batch = blockIdx.y, y0 = blockIdx.x * NB;
   const int H = bl.H, W = bl.W, ox = bl.ox;
@@ -83,7 +95,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
     return y < H ? __ldg(&src[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
-  I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
+  if constexpr (DB) I::rest2(v, u, buf, buf + P::BUF, tw);
+  else I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
   float2* dst = out + (size_t)batch * H * W;
   reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
     const int x = a - ox, y = y0 + b;
@@ -124,13 +137,15 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   using I = typename P::I;
   static_assert(I::C == F::A, "inverse must end where the forward starts");
   static_assert(T % 32 == 0, "the loss reduction shuffles over whole warps");
+  constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
   extern __shared__ float2 buf[];
   __shared__ float red[32];
   const int batch = blockIdx.y, y0 = blockIdx.x * NB;  // batch = l * C + c
   const int H = bl.H, W = bl.W, ox = bl.ox;
   float2* half = V + (size_t)batch * H * N;
   const float* tg = target + (size_t)batch * H * W;
-  float* tsm = reinterpret_cast<float*>(buf + P::BUF);
+  float2* by = buf + P::BUF;  // second exchange buffer (DB)
+  float* tsm = reinterpret_cast<float*>(buf + P::BUF + (DB ? P::BUF2 : 0));
   if (tstage) {
     const int chunks = NB * (W / 4);
     for (int i = threadIdx.x; i < chunks; i += T) {
@@ -145,7 +160,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     return y < H ? __ldg(&half[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
-  I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
+  if constexpr (DB) I::rest2(v, u, buf, by, tw);
+  else I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
   if (tstage) {
     cp_async_wait_all();
     __syncthreads();
@@ -171,7 +187,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     reg::first_in_regs<N, F::A, NB, T, false>(u);
     float2 w[F::GC::MB][F::C];
     // block_sum's barriers follow the inverse transform's last reads of buf
-    F::template rest<false>(u, w, buf, tw);
+    if constexpr (DB) F::rest2(u, w, buf, by, tw);
+    else F::template rest<false>(u, w, buf, tw);
     reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
       const int y = y0 + b;
       if (y < H) half[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
@@ -357,32 +374,36 @@ inline cudaError_t reg_set_smem(K kernel, size_t bytes, int resident) {
 template <int N, int R0, int R1, int R2, int NB, int CB, int T>
 cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, cudaStream_t s) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
+  constexpr size_t smem_db =
+      P::SMEM + (P::db_rows_fits(CGH_REG_MINB(T), 0) ? sizeof(float2) * (size_t)P::BUF2 : 0);
   dim3 grid((p->H + NB - 1) / NB, a->batches);
   const float2* tw = p->fx.tw;
   cudaError_t e = cudaSuccess;
   switch (kind) {
     case SPEC_ROWS_PAD_FWD: {
       auto k = kr_rows_pad_fwd<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, P::SMEM, CGH_REG_MINB(T));
+      e = reg_set_smem(k, smem_db, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_PAD_FWD, s);
-      k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->in, a->out);
+      k<<<grid, T, smem_db, s>>>(p->bl, tw, a->in, a->out);
       prof_end(KID_ROWS_PAD_FWD, s);
       break;
     }
     case SPEC_ROWS_INV_CROP: {
       auto k = kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, P::SMEM, CGH_REG_MINB(T));
+      e = reg_set_smem(k, smem_db, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_INV_CROP, s);
-      k<<<grid, T, P::SMEM, s>>>(p->bl, tw, a->in, a->out);
+      k<<<grid, T, smem_db, s>>>(p->bl, tw, a->in, a->out);
       prof_end(KID_ROWS_INV_CROP, s);
       break;
     }
     default: {
       const int tstage = (p->W % 4 == 0 && (reinterpret_cast<uintptr_t>(a->target) & 15u) == 0);
       auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
-      const size_t smem = P::SMEM + (tstage ? sizeof(float) * (size_t)NB * p->W : 0);
+      constexpr bool db = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
+      const size_t smem = P::SMEM + (db ? sizeof(float2) * (size_t)P::BUF2 : 0) +
+                          (tstage ? sizeof(float) * (size_t)NB * p->W : 0);
       e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_LOSS, s);
