@@ -39,10 +39,11 @@ struct RegPlan {
   static constexpr bool db_fits(int resident) {
     return (size_t)resident * (SMEM_SLOTS_DB + 1024) <= (size_t)228 * 1024;
   }
-  // row kernels: exchange buffers (+ `extra` bytes of staging) without slots
+  // row kernels: exchange buffers (+ `extra` bytes of staging) without slots; only for
+  // CTAs of several rows (single-row CTAs measured slower with the smaller L1 it leaves)
   static constexpr bool db_rows_fits(int resident, size_t extra) {
-    return (size_t)resident * (SMEM + sizeof(E) * (size_t)BUF2 + extra + 1024) <=
-           (size_t)228 * 1024;
+    return NB >= 2 && (size_t)resident * (SMEM + sizeof(E) * (size_t)BUF2 + extra + 1024) <=
+                          (size_t)228 * 1024;
   }
 };
 
