@@ -211,6 +211,8 @@ class Plan:
         self.aperture = float(aperture)
         self.max_gaussians = int(max_gaussians)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         lam = (ctypes.c_double * self.C)(*self.wavelengths_m)
         zz = (ctypes.c_double * self.L)(*self.z_m)
         h = ctypes.c_void_p()
