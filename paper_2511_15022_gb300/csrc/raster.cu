@@ -164,15 +164,16 @@ __global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__
 
 // Exclusive scan of tile counts (one CTA of 1024 threads).  tile_start has T+1 entries;
 // tile_count is reset to zero so that k_emit can use it as the per-tile cursor.
-// Each thread owns a contiguous chunk of `per` tiles.  STAGED: the counts pass through
-// shared memory (dynamic, scan_stage_ints(T) ints), so that global memory is read and
-// written with coalesced accesses -- with one CTA doing the whole scan, the chunked global
-// accesses would otherwise cost one L1 wavefront per thread per element.  The stage holds
-// element i at i + i / 32, which spreads a warp's chunk-wise accesses over all 32 banks.
+// The tiles are scanned in chunks of at most kScanChunk, each staged through shared memory
+// so that global memory is read and written with coalesced accesses (with one CTA doing the
+// whole scan, per-thread chunks read straight from global memory would cost one L1 wavefront
+// per thread per element).  Within a chunk each thread owns `per` consecutive tiles; the
+// stage holds element i at i + i / 32, which spreads a warp's chunk-wise accesses over all
+// 32 banks.  A running carry joins the chunks.
+constexpr int kScanChunk = 32768;
 __host__ __device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
-__host__ __device__ __forceinline__ size_t scan_stage_ints(int T) { return (size_t)scan_pad(T) + 1; }
+__host__ __device__ __forceinline__ size_t scan_stage_ints(int n) { return (size_t)scan_pad(n) + 1; }
 
-template <bool STAGED>
 __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
                                                      int* __restrict__ tile_count,
                                                      int* __restrict__ tile_start,
@@ -180,59 +181,56 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   extern __shared__ int stage[];
   __shared__ long long warp_sums[32];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int per = (T + nt - 1) / nt;
-  const int beg = min(T, tid * per), end = min(T, beg + per);
-  if (STAGED) {
-    for (int i = tid; i < T; i += nt) stage[scan_pad(i)] = tile_count[i * CGH_COUNT_STRIDE];
-    __syncthreads();
-  }
-  long long local = 0;
-  for (int i = beg; i < end; ++i) local += STAGED ? stage[scan_pad(i)] : tile_count[i * CGH_COUNT_STRIDE];
-  // inclusive scan of `local` over the CTA
-  long long v = local;
   const int lane = tid & 31, wid = tid >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    long long u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
-  }
-  if (lane == 31) warp_sums[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    long long w = (lane < (nt >> 5)) ? warp_sums[lane] : 0;
-    for (int o = 1; o < 32; o <<= 1) {
-      long long u = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += u;
-    }
-    warp_sums[lane] = w;
-  }
-  __syncthreads();
-  long long excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
-  // exclusive starts replace the counts (in the stage) or go straight to global memory
-  for (int i = beg; i < end; ++i) {
-    const int c = STAGED ? stage[scan_pad(i)] : tile_count[i * CGH_COUNT_STRIDE];
-    const int st = (int)min(excl, (long long)0x7fffffff);
-    if (STAGED) {
-      stage[scan_pad(i)] = st;
-    } else {
-      tile_start[i] = st;
-      tile_count[i * CGH_COUNT_STRIDE] = 0;
-    }
-    excl += c;
-  }
-  if (tid == nt - 1) {
-    tile_start[T] = (int)min(excl, (long long)0x7fffffff);
-    status[ST_PAIRS_LO] = (int)(excl & 0xffffffff);
-    status[ST_PAIRS_HI] = (int)(excl >> 32);
-    if (excl > cap) status[ST_OVERFLOW] = 1;
-  }
-  if (STAGED) {
+  long long carry = 0;  // pairs of the chunks before this one
+  for (int c0 = 0; c0 < T; c0 += kScanChunk) {
+    const int n = min(kScanChunk, T - c0);
+    __syncthreads();  // the previous chunk's stage has been written out
+    for (int i = tid; i < n; i += nt) stage[scan_pad(i)] = tile_count[(size_t)(c0 + i) * CGH_COUNT_STRIDE];
     __syncthreads();
-    for (int i = tid; i < T; i += nt) {
-      tile_start[i] = stage[scan_pad(i)];
-      tile_count[i * CGH_COUNT_STRIDE] = 0;  // k_emit's per-tile cursor
+    const int per = (n + nt - 1) / nt;
+    const int beg = min(n, tid * per), end = min(n, beg + per);
+    long long local = 0;
+    for (int i = beg; i < end; ++i) local += stage[scan_pad(i)];
+    // inclusive scan of `local` over the CTA
+    long long v = local;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
     }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      long long w = (lane < (nt >> 5)) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        long long u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    // exclusive starts replace the counts in the stage
+    long long excl = carry + v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+    for (int i = beg; i < end; ++i) {
+      const int c = stage[scan_pad(i)];
+      stage[scan_pad(i)] = (int)min(excl, (long long)0x7fffffff);
+      excl += c;
+    }
+    carry += warp_sums[(nt >> 5) - 1];
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+      tile_start[c0 + i] = stage[scan_pad(i)];
+      tile_count[(size_t)(c0 + i) * CGH_COUNT_STRIDE] = 0;  // k_emit's per-tile cursor
+    }
+  }
+  if (tid == 0) {
+    tile_start[T] = (int)min(carry, (long long)0x7fffffff);
+    status[ST_PAIRS_LO] = (int)(carry & 0xffffffff);
+    status[ST_PAIRS_HI] = (int)(carry >> 32);
+    if (carry > cap) status[ST_OVERFLOW] = 1;
   }
 }
+
 // The (Gaussian, tile) slots of one Gaussian: its cursor increments are issued in groups
 // of up to 8 tiles before any result is used, so their round trips overlap.
 __global__ void k_emit(RasterConsts rc, const int4* __restrict__ rect,
@@ -569,9 +567,6 @@ static RasterConsts make_consts(const cgh_plan* p, int N) {
   return rc;
 }
 
-// largest tile-count stage of k_scan_tiles (about 48K tiles: a 3072 x 4096 image at 16 x 16)
-constexpr size_t kScanStageBytes = 200 * 1024;
-
 // Binning shared by forward and backward: preprocess, scan, emit.
 static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   const int T = p->tiles_x * p->tiles_y;
@@ -599,20 +594,15 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
     prof_end(KID_PREPROCESS, s);
   }
   prof_begin(KID_SCAN_TILES, s);
-  const size_t stage_bytes = sizeof(int) * scan_stage_ints(T);
-  if (stage_bytes <= kScanStageBytes) {
-    static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_scan_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kScanStageBytes);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_scan_tiles<true><<<1, 1024, stage_bytes, s>>>(T, p->pair_capacity, tile_count, tile_start,
-                                                    status);
-  } else {
-    k_scan_tiles<false><<<1, 1024, 0, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
+  const size_t stage_bytes = sizeof(int) * scan_stage_ints(T < kScanChunk ? T : kScanChunk);
+  static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_scan_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(int) * scan_stage_ints(kScanChunk)));
+    if (e != cudaSuccess) return e;
+    attr = true;
   }
+  k_scan_tiles<<<1, 1024, stage_bytes, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
   prof_end(KID_SCAN_TILES, s);
   if (prm->N > 0) {
     prof_begin(KID_EMIT, s);

@@ -52,6 +52,28 @@ def test_raster_fwd(name, dev):
     assert rel_l2(U, ref) < FIELD_TOL
 
 
+def test_raster_with_more_tiles_than_one_scan_chunk(dev):
+    """2304 x 4096 pixels = 36,864 tiles: the tile scan runs in two chunks joined by a
+    carry; the field on sampled pixels (all of the first and last tile rows included) and
+    the gradients of sampled Gaussians against the oracle."""
+    import torch
+    w = inputs.custom(2304, 4096, 6000, seed=41)
+    p = inputs.params_for(w)
+    plan = make_plan(w, dev)
+    U = c64(plan.raster_fwd(to_dev(p, dev))).reshape(w.C, -1)
+    rows = np.concatenate([np.arange(0, 16), np.arange(w.H - 16, w.H)])
+    edge = (rows[:, None] * w.W + np.arange(0, w.W, 7)[None, :]).reshape(-1)
+    idx = np.unique(np.concatenate([inputs.sample_indices(3000, w.H * w.W, seed=42), edge]))
+    ref = oracle.raster_fwd(to64(p), w.H, w.W, w.cutoff, pix_idx=idx)
+    assert rel_l2(U[:, idx], ref) < FIELD_TOL
+    dU = inputs.random_field(w.C, w.H, w.W, seed=43)
+    g = plan.raster_bwd(to_dev(p, dev), torch.from_numpy(dU).to(dev))
+    sel = inputs.sample_indices(16, w.N, seed=44)
+    gref = oracle.raster_bwd(to64(p), w.H, w.W, dU, w.cutoff, g_idx=sel)
+    for k in gref:
+        assert rel_l2(g[k].double().cpu().numpy()[sel], gref[k]) < GRAD_TOL, k
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_blasm_fwd_bwd(name, dev):
     import torch
