@@ -228,13 +228,61 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def oracle_sample(w, params_np, target_np, budget_s: float = 4.0) -> dict:
+def prop_crop(w, budget_s: float) -> int:
+    """Divisor of the image sides for the propagation sample of oracle_sample."""
+    f = min(1.0, budget_s / 4.0)
+    return 1 if f >= 1.0 else 2 if f >= 0.25 else 4 if f >= 0.06 else 8
+
+
+def prop_scale_measured(w, budget_s: float) -> float:
+    """Measured ratio of one full channel-plane propagation of the oracle to the central
+    crop oracle_sample times at this budget (1 when no crop is used)."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_15022_gb300 import inputs
+    div = prop_crop(w, budget_s)
+    if div == 1:
+        return 1.0
+    dU = inputs.random_field(1, w.H, w.W, seed=7).astype(np.complex128)
+    h, wd = w.H // div, w.W // div
+    crop = np.ascontiguousarray(dU[:, (w.H - h) // 2:(w.H - h) // 2 + h,
+                                   (w.W - wd) // 2:(w.W - wd) // 2 + wd])
+    t0 = time.perf_counter()
+    oracle.blasm_fwd(dU, [w.wavelengths_m[0]], w.pitch_m, [w.z_m[-1]], w.pad)
+    t_full = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.blasm_fwd(crop, [w.wavelengths_m[0]], w.pitch_m, [w.z_m[-1]], w.pad)
+    return t_full / (time.perf_counter() - t0)
+
+
+def oracle_fixed_costs(w, params_np) -> dict:
+    """Per-call fixed costs of the oracle's raster forward and backward (parameter
+    conversion, thread start-up), measured on a one-pixel and a one-Gaussian sample; small
+    samples subtract them before scaling up."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_15022_gb300 import inputs
+    p64 = {k: v.astype(np.float64) for k, v in params_np.items()}
+    dU = inputs.random_field(w.C, w.H, w.W, seed=7).astype(np.complex128)
+    t0 = time.perf_counter()
+    oracle.raster_fwd(p64, w.H, w.W, w.cutoff, pix_idx=np.array([0]))
+    t1 = time.perf_counter()
+    oracle.raster_bwd(p64, w.H, w.W, dU, w.cutoff, g_idx=np.array([0]))
+    t2 = time.perf_counter()
+    return {"fwd": t1 - t0, "bwd": t2 - t1}
+
+
+def oracle_sample(w, params_np, target_np, budget_s: float = 4.0,
+                  prop_scale: float = None, fixed: dict = None) -> dict:
     """Time the FP64 oracle on a bounded sample of one step and extrapolate to a full step:
     raster forward on a pixel sample, raster backward on a Gaussian sample (all pixels),
     and one channel-plane propagation (pad, FFT2, H, IFFT2, crop) of the full field or, for
-    small budgets, of a central crop scaled by area x log2(padded size); the propagation
-    time counts for the C*L forward + C*L adjoint propagations of a step.  The sample sizes
-    scale with budget_s (about 4 s of host work for the default sizes)."""
+    small budgets, of a central crop scaled by `prop_scale` (full / crop time, measured in
+    the same run; by area x log2(padded size) if not given); the propagation time counts
+    for the C*L forward + C*L adjoint propagations of a step.  The sample sizes scale with
+    budget_s (about 4 s of host work for the default sizes)."""
     import math
 
     import numpy as np
@@ -246,16 +294,19 @@ def oracle_sample(w, params_np, target_np, budget_s: float = 4.0) -> dict:
     f = min(1.0, budget_s / 4.0)
     npix = max(64, int(6000 * f))
     idx = inputs.sample_indices(npix, HW, seed=5)
+    fx = fixed or {"fwd": 0.0, "bwd": 0.0}
     t0 = time.perf_counter()
     oracle.raster_fwd(p64, w.H, w.W, w.cutoff, pix_idx=idx)
-    t_fwd = (time.perf_counter() - t0) * HW / npix
+    t = time.perf_counter() - t0
+    t_fwd = max(t - fx["fwd"], 0.0) * HW / npix + fx["fwd"]
     ng = max(4, int(48 * f))
     sel = inputs.sample_indices(ng, w.N, seed=6)
     dU = inputs.random_field(w.C, w.H, w.W, seed=7).astype(np.complex128)
     t0 = time.perf_counter()
     oracle.raster_bwd(p64, w.H, w.W, dU, w.cutoff, g_idx=sel)
-    t_bwd = (time.perf_counter() - t0) * w.N / ng
-    div = 1 if f >= 1.0 else 2 if f >= 0.25 else 4 if f >= 0.06 else 8
+    t = time.perf_counter() - t0
+    t_bwd = max(t - fx["bwd"], 0.0) * w.N / ng + fx["bwd"]
+    div = prop_crop(w, budget_s)
     h, wd = w.H // div, w.W // div
     crop = np.ascontiguousarray(dU[:1, (w.H - h) // 2:(w.H - h) // 2 + h,
                                    (w.W - wd) // 2:(w.W - wd) // 2 + wd])
@@ -263,13 +314,21 @@ def oracle_sample(w, params_np, target_np, budget_s: float = 4.0) -> dict:
     oracle.blasm_fwd(crop, [w.wavelengths_m[0]], w.pitch_m, [w.z_m[-1]], w.pad)
     t_crop = time.perf_counter() - t0
     n_full, n_crop = (w.pad * w.H) * (w.pad * w.W), (w.pad * h) * (w.pad * wd)
-    t_prop = t_crop * (n_full / n_crop) * math.log2(n_full) / math.log2(n_crop)
+    if div == 1:
+        t_prop, how = t_crop, ""
+    elif prop_scale is not None:
+        t_prop, how = t_crop * prop_scale, f"scaled by the measured full/crop ratio {prop_scale:.1f}"
+    else:
+        t_prop = t_crop * (n_full / n_crop) * math.log2(n_full) / math.log2(n_crop)
+        how = "scaled by area x log"
     t_step = t_fwd + t_bwd + 2 * w.C * w.L * t_prop
-    prop_txt = ("1" if div == 1 else f"a central {h}x{wd} crop (scaled by area x log) of 1")
+    prop_txt = ("1" if div == 1 else f"a central {h}x{wd} crop ({how}) of 1")
+    fixed_txt = (f" (per-call fixed costs {fx['fwd']:.3f} / {fx['bwd']:.3f} s measured and not "
+                 f"scaled)" if fixed else "")
     return {"value": 1.0 / t_step, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"FP64 oracle, extrapolated: raster fwd on {npix} of {HW} pixels, raster "
-                       f"bwd on {ng} of {w.N} Gaussians, {prop_txt} of {2 * w.C * w.L} "
-                       f"channel-plane propagations; est. {t_step:.1f} s/step")}
+                       f"bwd on {ng} of {w.N} Gaussians{fixed_txt}, {prop_txt} of "
+                       f"{2 * w.C * w.L} channel-plane propagations; est. {t_step:.1f} s/step")}
 
 
 # ------------------------------------------------------------------ torch / cuFFT baseline
@@ -924,11 +983,13 @@ def main():
         target_np = inputs.blob_targets(w.L, w.C, w.H, w.W)
         # each step a bounded sample: the whole run takes about 150 s of host work
         budget = min(4.0, 150.0 / max(1, args.steps + args.warmup))
+        scale = prop_scale_measured(w, budget)
+        fixed = oracle_fixed_costs(w, params_np) if budget < 4.0 else None
         vals = []
         for _ in range(args.warmup):
-            oracle_sample(w, params_np, target_np, budget)
+            oracle_sample(w, params_np, target_np, budget, scale, fixed)
         for _ in range(args.steps):
-            r = oracle_sample(w, params_np, target_np, budget)
+            r = oracle_sample(w, params_np, target_np, budget, scale, fixed)
             vals.append(r["value"])
         v = statistics.median(vals)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
