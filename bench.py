@@ -1034,7 +1034,7 @@ def learned_init_bench(dev, full: bool = False) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="autograd", choices=["autograd", "fused"])
@@ -1263,7 +1263,7 @@ def main():
             "autotuned": tuned is not None,
         }
         if not args.no_extras and world == 1:
-            line["batched"] = batched_bench(dev, steps=max(5, args.steps // 4), warmup=3)
+            line["batched"] = batched_bench(dev, steps=min(50, max(5, args.steps // 4)), warmup=3)
             line["batched_time_to_psnr"] = batched_time_to_psnr(
                 dev, line["batched"]["it_per_s_separate_launches"])
             line["time_to_psnr"] = time_to_psnr(dev, plan_tuning=tuned)
