@@ -256,22 +256,41 @@ def prop_scale_measured(w, budget_s: float) -> float:
     return t_full / (time.perf_counter() - t0)
 
 
-def oracle_fixed_costs(w, params_np) -> dict:
-    """Per-call fixed costs of the oracle's raster forward and backward (parameter
-    conversion, thread start-up), measured on a one-pixel and a one-Gaussian sample; small
-    samples subtract them before scaling up."""
+def oracle_sample_sizes(w, budget_s: float) -> tuple:
+    """(pixels, Gaussians) that oracle_sample times at this budget: at least 64 pixels and
+    one Gaussian per host thread, so that small samples still keep every core busy."""
+    import oracle
+    f = min(1.0, budget_s / 4.0)
+    threads = max(1, oracle.num_threads())
+    return max(64 * threads, int(6000 * f)), max(threads, int(48 * f))
+
+
+def oracle_fixed_costs(w, params_np, budget_s: float) -> dict:
+    """Per-call fixed costs of the oracle's raster forward and backward at the sample sizes
+    of this budget, from a two-point fit t(n) = a + b n over the sample and four times it;
+    small samples subtract a before scaling up."""
     import numpy as np
 
     import oracle
     from paper_2511_15022_gb300 import inputs
     p64 = {k: v.astype(np.float64) for k, v in params_np.items()}
     dU = inputs.random_field(w.C, w.H, w.W, seed=7).astype(np.complex128)
-    t0 = time.perf_counter()
-    oracle.raster_fwd(p64, w.H, w.W, w.cutoff, pix_idx=np.array([0]))
-    t1 = time.perf_counter()
-    oracle.raster_bwd(p64, w.H, w.W, dU, w.cutoff, g_idx=np.array([0]))
-    t2 = time.perf_counter()
-    return {"fwd": t1 - t0, "bwd": t2 - t1}
+    npix, ng = oracle_sample_sizes(w, budget_s)
+
+    def t_fwd(n):
+        idx = inputs.sample_indices(n, w.H * w.W, seed=5)
+        t0 = time.perf_counter()
+        oracle.raster_fwd(p64, w.H, w.W, w.cutoff, pix_idx=idx)
+        return time.perf_counter() - t0
+
+    def t_bwd(n):
+        sel = inputs.sample_indices(n, w.N, seed=6)
+        t0 = time.perf_counter()
+        oracle.raster_bwd(p64, w.H, w.W, dU, w.cutoff, g_idx=sel)
+        return time.perf_counter() - t0
+
+    return {"fwd": max(0.0, (4 * t_fwd(npix) - t_fwd(4 * npix)) / 3),
+            "bwd": max(0.0, (4 * t_bwd(ng) - t_bwd(4 * ng)) / 3)}
 
 
 def oracle_sample(w, params_np, target_np, budget_s: float = 4.0,
@@ -291,15 +310,13 @@ def oracle_sample(w, params_np, target_np, budget_s: float = 4.0,
     from paper_2511_15022_gb300 import inputs
     p64 = {k: v.astype(np.float64) for k, v in params_np.items()}
     HW = w.H * w.W
-    f = min(1.0, budget_s / 4.0)
-    npix = max(64, int(6000 * f))
+    npix, ng = oracle_sample_sizes(w, budget_s)
     idx = inputs.sample_indices(npix, HW, seed=5)
     fx = fixed or {"fwd": 0.0, "bwd": 0.0}
     t0 = time.perf_counter()
     oracle.raster_fwd(p64, w.H, w.W, w.cutoff, pix_idx=idx)
     t = time.perf_counter() - t0
     t_fwd = max(t - fx["fwd"], 0.0) * HW / npix + fx["fwd"]
-    ng = max(4, int(48 * f))
     sel = inputs.sample_indices(ng, w.N, seed=6)
     dU = inputs.random_field(w.C, w.H, w.W, seed=7).astype(np.complex128)
     t0 = time.perf_counter()
@@ -1066,7 +1083,7 @@ def main():
         # each step a bounded sample: the whole run takes about 150 s of host work
         budget = min(4.0, 150.0 / max(1, args.steps + args.warmup))
         scale = prop_scale_measured(w, budget)
-        fixed = oracle_fixed_costs(w, params_np) if budget < 4.0 else None
+        fixed = oracle_fixed_costs(w, params_np, budget) if budget < 4.0 else None
         vals = []
         for _ in range(args.warmup):
             oracle_sample(w, params_np, target_np, budget, scale, fixed)
