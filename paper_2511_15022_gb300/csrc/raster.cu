@@ -231,28 +231,54 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
   }
 }
 
-// The (Gaussian, tile) slots of one Gaussian: its cursor increments are issued in groups
-// of up to 8 tiles before any result is used, so their round trips overlap.
-__global__ void k_emit(RasterConsts rc, const int4* __restrict__ rect,
-                       const int* __restrict__ tile_start, int* __restrict__ cursor,
-                       int* __restrict__ pairs) {
+// The (Gaussian, tile) slots.  A warp pools the boxes of its 32 Gaussians and deals the
+// (Gaussian, tile) items out to its lanes, EMIT_U per lane per round, so that one large box
+// (optimised Gaussians can grow to cover a hundred tiles) costs its warp a few rounds instead
+// of a long serial loop in one lane; each round's cursor increments are all in flight at once.
+constexpr int EMIT_U = 4;
+__global__ void __launch_bounds__(256) k_emit(RasterConsts rc, const int4* __restrict__ rect,
+                                              const int* __restrict__ tile_start,
+                                              int* __restrict__ cursor, int* __restrict__ pairs) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= rc.N) return;
-  const int4 r = __ldg(&rect[n]);
-  const int bw = r.z - r.x + 1, cnt = (r.z >= r.x && r.w >= r.y) ? bw * (r.w - r.y + 1) : 0;
-  for (int k0 = 0; k0 < cnt; k0 += 8) {
-    int t[8], slot[8];
+  const int lane = threadIdx.x & 31;
+  int4 r = make_int4(1, 1, 0, 0);
+  if (n < rc.N) r = __ldg(&rect[n]);
+  const int bw = r.z - r.x + 1;
+  const int cnt = (r.z >= r.x && r.w >= r.y) ? bw * (r.w - r.y + 1) : 0;
+  // exclusive prefix of the box sizes over the warp
+  int incl = cnt;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int kk = k0 + k;
-      t[k] = kk < cnt ? (r.y + kk / bw) * rc.tiles_x + r.x + kk % bw : -1;
-      slot[k] = t[k] >= 0 ? atomicAdd(&cursor[t[k] * CGH_COUNT_STRIDE], 1) : 0;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  const int excl = incl - cnt;
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int warp_n0 = n - lane;
+  for (int k0 = 0; k0 < total; k0 += 32 * EMIT_U) {
+    int t[EMIT_U], slot[EMIT_U], gid[EMIT_U];
+#pragma unroll
+    for (int u = 0; u < EMIT_U; ++u) {
+      const int k = k0 + u * 32 + lane;
+      // owner: the last lane whose exclusive prefix is <= k (it holds item k when k < total)
+      int o = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, excl, o + step);
+        if (e <= k) o += step;
+      }
+      const int j = k - __shfl_sync(0xffffffffu, excl, o);
+      const int obw = __shfl_sync(0xffffffffu, bw, o);
+      const int ox = __shfl_sync(0xffffffffu, r.x, o), oy = __shfl_sync(0xffffffffu, r.y, o);
+      gid[u] = warp_n0 + o;
+      t[u] = k < total ? (oy + j / obw) * rc.tiles_x + ox + j % obw : -1;
+      slot[u] = t[u] >= 0 ? atomicAdd(&cursor[t[u] * CGH_COUNT_STRIDE], 1) : 0;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (t[k] < 0) continue;
-      const long long pos = (long long)__ldg(&tile_start[t[k]]) + slot[k];
-      if (pos < rc.cap) pairs[pos] = n;
+    for (int u = 0; u < EMIT_U; ++u) {
+      if (t[u] < 0) continue;
+      const long long pos = (long long)__ldg(&tile_start[t[u]]) + slot[u];
+      if (pos < rc.cap) pairs[pos] = gid[u];
     }
   }
 }
