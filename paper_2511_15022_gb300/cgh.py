@@ -234,8 +234,9 @@ class Plan:
         _check(_lib.cgh_plan_workspace_bytes(self._h, ctypes.byref(n)), "workspace_bytes")
         if self._ws is None or self._ws.numel() < n.value:
             self._ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.device)
-        _check(_lib.cgh_plan_set_workspace(self._h, ctypes.c_void_p(self._ws.data_ptr()),
-                                           self._ws.numel()), "set_workspace")
+        with torch.cuda.device(self.device):  # the library zeroes status words on this device
+            _check(_lib.cgh_plan_set_workspace(self._h, ctypes.c_void_p(self._ws.data_ptr()),
+                                               self._ws.numel()), "set_workspace")
 
     @property
     def workspace_bytes(self) -> int:
@@ -246,7 +247,8 @@ class Plan:
     def set_tuning(self, col_block=0, row_block=0, fft_threads=0, pair_capacity_per_gaussian=0,
                    fft_kernels=0):
         t = _Tuning(col_block, row_block, fft_threads, pair_capacity_per_gaussian, fft_kernels)
-        _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
+        with torch.cuda.device(self.device):
+            _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
         if self._ws is not None:
             self._attach_workspace()
 
