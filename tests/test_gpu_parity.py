@@ -52,6 +52,26 @@ def test_raster_fwd(name, dev):
     assert rel_l2(U, ref) < FIELD_TOL
 
 
+def test_raster_with_gaussians_spanning_hundreds_of_tiles(dev):
+    """Scales up to 40 px (boxes of up to ~16 x 16 tiles, the size optimised Gaussians grow
+    to): the tile emit deals each warp's pooled (Gaussian, tile) items to its lanes; field
+    and sampled gradients against the oracle."""
+    import torch
+    w = inputs.custom(384, 512, 700, s_min_px=0.5, s_max_px=40.0, seed=45)
+    p = inputs.params_for(w)
+    plan = make_plan(w, dev)
+    U = c64(plan.raster_fwd(to_dev(p, dev)))
+    ref = oracle.raster_fwd(to64(p), w.H, w.W, w.cutoff)
+    assert rel_l2(U, ref) < FIELD_TOL
+    dU = inputs.random_field(w.C, w.H, w.W, seed=46)
+    g = plan.raster_bwd(to_dev(p, dev), torch.from_numpy(dU).to(dev))
+    sel = inputs.sample_indices(24, w.N, seed=47)
+    gref = oracle.raster_bwd(to64(p), w.H, w.W, dU, w.cutoff, g_idx=sel)
+    for k in gref:
+        assert rel_l2(g[k].double().cpu().numpy()[sel], gref[k]) < GRAD_TOL, k
+    assert plan.status()["pairs"] > 8 * w.N  # many tiles per Gaussian on average
+
+
 def test_raster_with_more_tiles_than_one_scan_chunk(dev):
     """2304 x 4096 pixels = 36,864 tiles: the tile scan runs in two chunks joined by a
     carry; the field on sampled pixels (all of the first and last tile rows included) and
