@@ -183,10 +183,12 @@ RASTER_SOURCES = ("raster.cu", "cgh_internal.h")
 
 def kernel_source_sha(kernel: str = "") -> str:
     """Hash of the CUDA sources a kernel is built from (the FFT-pass files for k_rows_* /
-    k_cols_*, the rasteriser for k_raster_*, all of csrc otherwise): ncu traffic figures
-    are valid only for the kernel sources they were captured from."""
+    k_cols_*, the rasteriser for k_raster_*, all of csrc otherwise), comments and
+    whitespace removed: ncu traffic figures are valid only for the kernel code they were
+    captured from."""
     import glob
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_2511_15022_gb300", "csrc")
     if kernel.startswith(("k_rows_", "k_cols_")):
         files = [f for pat in FFT_SOURCES for f in glob.glob(os.path.join(csrc, pat))]
@@ -196,9 +198,13 @@ def kernel_source_sha(kernel: str = "") -> str:
         files = glob.glob(os.path.join(csrc, "*"))
     h = hashlib.sha256()
     for f in sorted(files):
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode())
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        code = re.sub(r"\s+", "", code)
+        h.update(os.path.basename(f).encode())
+        h.update(code.encode())
     return h.hexdigest()[:12]
 
 

@@ -6,10 +6,13 @@
 //   kr_cols_fwd_planes column slab -> FFT -> spectrum in registers -> for each plane
 //                      x H_{c,l}/(Ny Nx) -> inverse FFT -> cropped rows
 //   kr_rows_loss       inverse row FFT -> crop, |U|^2, loss partials, dL/dU seed in
-//                      registers -> forward row FFT -> in place
-//   kr_cols_bwd_planes for each plane: FFT -> x conj(H_{c,l})/(Ny Nx), accumulated in
-//                      registers -> one inverse FFT -> cropped rows
+//                      registers -> forward row FFT -> in place; the pass's last CTA sums
+//                      the partials into the loss
+//   kr_cols_bwd_planes for each plane: FFT -> x conj(H_{c,l}), accumulated in
+//                      thread-private shared-memory slots -> one inverse FFT -> cropped rows
 //   kr_rows_inv_crop   blocked half grid -> inverse FFT -> cropped image rows
+// Where two exchange buffers fit the resident CTAs, each transform alternates between them
+// (two barriers per transform instead of four).
 #pragma once
 
 #include "blasm_common.cuh"
