@@ -1074,6 +1074,10 @@ def main():
                                                  rank_info, replica_seed)
     ri = rank_info()
     rank, world, local_rank = ri.rank, ri.world, ri.local_rank
+    if args.gpus != world and rank == 0:
+        print(f"bench.py: --gpus {args.gpus} but {world} process(es); launch N > 1 with "
+              f"torchrun --nproc-per-node N (one process per GPU); measuring {world}",
+              file=sys.stderr)
 
     from paper_2511_15022_gb300 import inputs
     w = inputs.hd_1080p()
