@@ -1286,6 +1286,12 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "kernels": per_kernel, "clocks": clk,
+            # rasteriser work after the run's steps: the (Gaussian, 16x16 tile) list the
+            # kernels walk, and the estimated (pixel, Gaussian) pairs above the cutoff
+            "raster_pairs": {
+                "tile_list": plan.status()["pairs"],
+                "pixel_pairs_est": raster_pairs({k: v.detach().cpu().numpy()
+                                                 for k, v in params.items()}, w.cutoff)},
             "torch_cufft_blasm": torch_blasm_ms(w, dev) if not args.no_extras else None,
             "autotuned": tuned is not None,
         }
