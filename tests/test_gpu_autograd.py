@@ -157,3 +157,20 @@ def test_gradients_against_finite_differences_on_a_64x64_crop(dev):
             qm[key][idx] -= h
             fd = (loss(qp) - loss(qm)) / (2 * h)
             assert abs(gk[idx] - fd) <= 2e-3 * abs(fd) + floor, (key, idx, gk[idx], fd)
+
+
+def test_step_scaled_argument_checks(dev):
+    """The upstream scale must be one float32 element on the plan's device."""
+    import torch
+    w = inputs.custom(32, 48, 50, seed=48)
+    p = to_dev(inputs.params_for(w), dev)
+    T = torch.from_numpy(inputs.blob_targets(w.L, w.C, w.H, w.W)).to(dev)
+    plan = make_plan(w, dev)
+    for bad in (torch.ones(1, dtype=torch.float64, device=dev), torch.ones(2, device=dev),
+                torch.ones(1)):
+        with pytest.raises(ValueError):
+            plan.step(p, T, grad_scale=bad)
+    _, g0 = plan.step(p, T)
+    _, g2 = plan.step(p, T, grad_scale=torch.full((1,), 2.0, device=dev))
+    for k in g0:
+        assert torch.allclose(g2[k], 2.0 * g0[k], rtol=1e-5, atol=1e-12), k
