@@ -173,4 +173,4 @@ def test_step_scaled_argument_checks(dev):
     _, g0 = plan.step(p, T)
     _, g2 = plan.step(p, T, grad_scale=torch.full((1,), 2.0, device=dev))
     for k in g0:
-        assert torch.allclose(g2[k], 2.0 * g0[k], rtol=1e-5, atol=1e-12), k
+        assert rel_l2(g2[k].double().cpu().numpy(), 2.0 * g0[k].double().cpu().numpy()) < 1e-5, k
