@@ -1101,7 +1101,7 @@ def main():
             r = oracle_sample(w, params_np, target_np, budget, scale, fixed)
             vals.append(r["value"])
         v = statistics.median(vals)
-        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
