@@ -523,7 +523,7 @@ def poh_bench(dev, plan_tuning=None, iters: int = 300, phase_lr: float = 1e-2) -
 
     def nrmse(field):  # RMS intensity error over the mean target intensity, all planes
         with torch.no_grad():
-            Ip = plan.blasm_fwd(field).abs().square()
+            Ip = plan.intensity(plan.blasm_fwd(field))
             return round(float(((Ip - target) ** 2).mean().sqrt()) / tmean, 4)
 
     for _ in range(3):
@@ -808,9 +808,9 @@ def planted_target(plan, w, seed: int):
     planted_np["amp"] = np.ascontiguousarray(blob[:, ys, xs].T.astype(np.float32))
     planted_np["phase"][:] = 0.0
     planted = {k: torch.from_numpy(v).to(plan.device) for k, v in planted_np.items()}
-    I = plan.blasm_fwd(plan.raster_fwd(planted)).abs().square()
+    I = plan.intensity(plan.blasm_fwd(plan.raster_fwd(planted)))
     planted["amp"] *= math.sqrt(0.35 / float(I.mean()))
-    return plan.blasm_fwd(plan.raster_fwd(planted)).abs().square().contiguous()
+    return plan.intensity(plan.blasm_fwd(plan.raster_fwd(planted)))
 
 
 def batched_time_to_psnr(dev, it_per_s_separate: float, iters: int = 400,
@@ -846,7 +846,7 @@ def batched_time_to_psnr(dev, it_per_s_separate: float, iters: int = 400,
         out = []
         with torch.no_grad():
             for plan, p, t in zip(plans, params, targets):
-                I = plan.blasm_fwd(plan.raster_fwd(p)).abs().square().clamp(0, 1)
+                I = plan.intensity(plan.blasm_fwd(plan.raster_fwd(p))).clamp(0, 1)
                 mse = ((I - t.clamp(0, 1)) ** 2).mean(dim=(1, 2, 3))
                 out.append(float((10 * torch.log10(1.0 / mse)).mean()))
         return out
@@ -918,7 +918,7 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
     def psnr():
         with torch.no_grad():
             Ipred = plan.blasm_fwd(plan.raster_fwd({k: v.detach() for k, v in params.items()}))
-            Ipred = Ipred.abs().square().clamp(0, 1)
+            Ipred = plan.intensity(Ipred).clamp(0, 1)
             mse = ((Ipred - target.clamp(0, 1)) ** 2).mean(dim=(1, 2, 3))
             return float((10 * torch.log10(1.0 / mse)).mean())
 

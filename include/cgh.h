@@ -166,7 +166,11 @@ cgh_status cgh_raster_fwd(cgh_plan* plan, const cgh_params* params, void* U_out,
  * device looks up the array's device address (cudaGetSymbolAddress), so make that first
  * call before any stream capture.  All calls share the one array: calls whose GPU work
  * overlaps (different streams, or concurrent host threads) race and corrupt each other's
- * results; order them on one stream. */
+ * results; order them on one stream.  The call works on the CURRENT device (the caller makes
+ * the device that holds params and U_out current).  Having no plan, it has no status to
+ * report through cgh_plan_status: Gaussians with a non-finite parameter are skipped without
+ * notice, and when the (Gaussian, tile) list outgrows the space left in the array the tiles
+ * past it fall back, silently, to the slower exhaustive path (the field stays exact). */
 cgh_status cgh_raster_fwd_noalloc(int32_t H, int32_t W, int32_t C, float cutoff,
                                   const cgh_params* params, void* U_out, void* stream);
 
@@ -191,6 +195,19 @@ cgh_status cgh_blasm_bwd(cgh_plan* plan, const void* dUd, void* dU0_out, void* s
  * / (L*C*H*W) * Ud.  Ud: [L][C][H][W] complex; target: [L][C][H][W] float. */
 cgh_status cgh_intensity_loss(cgh_plan* plan, const void* Ud, const float* target,
                               float* loss_out, void* dUd_out, void* stream);
+
+/* Intensity of the propagated fields (Sec. 3.2, I_l = |U(d_l)|^2):
+ *   I_out[i] = Re(Ud[i])^2 + Im(Ud[i])^2 for the L*C*H*W values of the plan's geometry.
+ * Ud: [L][C][H][W] complex (e.g. the output of cgh_blasm_fwd); I_out: [L][C][H][W] float.
+ * For losses defined by the caller on the intensities. */
+cgh_status cgh_intensity(cgh_plan* plan, const void* Ud, float* I_out, void* stream);
+
+/* Adjoint of cgh_intensity (chain rule of I = |U|^2 in the gradient convention of the
+ * supplementary, dL/dU = dL/dRe + j dL/dIm):  dUd_out[i] = 2 dI[i] Ud[i].
+ * Ud: [L][C][H][W] complex (the same field); dI = dL/dI: [L][C][H][W] float;
+ * dUd_out: [L][C][H][W] complex (may be fed to cgh_blasm_bwd). */
+cgh_status cgh_intensity_bwd(cgh_plan* plan, const void* Ud, const float* dI, void* dUd_out,
+                             void* stream);
 
 /* Forward only: raster -> BLASM -> loss (loss_out: device float[1]).  Nothing but the
  * workspace is written. */

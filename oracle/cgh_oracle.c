@@ -16,15 +16,23 @@
  *   - Adam (PyTorch semantics)
  * No tiling, no culling, no fusion: every pixel meets every Gaussian.
  *
- * Readings of the paper where it is silent (numbered as in the design notes):
- *   pixel centres are 0-based integers (O-4); zero-pad is centred with offset (N-n)/2 (O-3);
- *   frequency of FFT bin k is s(k)/(N*pitch) with s(k)=k for k<N/2 else k-N, which is the
- *   centred index i-N/2 of Algorithm 3 after an fftshift (O-2); the band limit is the
- *   rectangular one of Algorithm 3 with L = padded extent (O-1, O-2); the clamped pairs
- *   (alpha*G > 0.99) pass no gradient to alpha, mean and covariance, skipped pairs pass none
- *   at all (O-6); the inverse-covariance to covariance step, absent from the paper, is the
- *   exact derivative of the adjugate formula (O-13); the loss is the mean over C*H*W, times
- *   1/L (O-7).
+ * Readings of the paper where it is silent, ambiguous or inconsistent:
+ *   - pixel centres are the 0-based integers 0..W-1, 0..H-1 (Sec. 3.1 counts pixels from 1
+ *     while the means live in [0, W]; the difference is a reparametrisation);
+ *   - the zero-pad of Algorithm 1 is 2x and centred, the image at offset (N-n)/2 per axis,
+ *     and the crop takes the same window back;
+ *   - the frequency of FFT bin k is s(k)/(N*pitch) with s(k)=k for k<N/2 else k-N, which is
+ *     the centred index i-N/2 of Algorithm 3 after an fftshift;
+ *   - the band limit is the rectangular one of Algorithm 3 (not the circular cut of the
+ *     Sec. 2 equation), with the extent L taken on the PADDED grid (the propagation step
+ *     of Algorithm 1 receives the padded field);
+ *   - pairs with alpha*G above 0.99 are clamped and pass no gradient to alpha, mean and
+ *     covariance (amplitude and phase still get 0.99 * ...); pairs below the 1/255 skip
+ *     threshold pass none at all (the forward of Algorithm 2 differentiated as written);
+ *   - the inverse-covariance to covariance step, absent from the paper's gradients, is the
+ *     exact derivative of the adjugate formula inv = (S11, -S01, S00) / det;
+ *   - the loss is the mean over the C*H*W values of each plane, times 1/L (Sec. 3.2 prints
+ *     an unnormalised squared norm).
  *
  * Layouts: params are structure-of-arrays: xy_raw[N][2], s_raw[N][2], theta[N], amp[N][C],
  * phase[N][C], alpha_raw[N].  Complex fields are interleaved (re, im) doubles, [C][H][W].

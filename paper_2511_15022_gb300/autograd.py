@@ -11,8 +11,9 @@ have changed: autograd rejects in-place changes to them).  With eager=True the f
 O(N) parameter gradients instead (no recompute; still no per-pixel state).
 
 HologramIntensity returns I_l = |U(d_l)|^2 [L, C, H, W] for user-defined losses; its
-backward recomputes the field and chains dL/dI through the adjoint propagation and the
-raster backward.
+backward recomputes the field and chains dL/dI through the intensity adjoint
+(cgh_intensity_bwd), the adjoint propagation and the raster backward.  Every arithmetic
+step of both runs in the library's kernels; this module only orders the calls.
 """
 from __future__ import annotations
 
@@ -71,16 +72,15 @@ class HologramIntensity(torch.autograd.Function):
         p = _params(tensors)
         ctx.plan = plan
         ctx.save_for_backward(*[p[k] for k in PARAM_KEYS])
-        Ud = plan.blasm_fwd(plan.raster_fwd(p))
-        return Ud.abs().square()
+        return plan.intensity(plan.blasm_fwd(plan.raster_fwd(p)))
 
     @staticmethod
     def backward(ctx, dI):
         plan = ctx.plan
         p = dict(zip(PARAM_KEYS, ctx.saved_tensors))
         Ud = plan.blasm_fwd(plan.raster_fwd(p))
-        dUd = (2.0 * dI.contiguous()) * Ud  # dL/dRe + j dL/dIm = 2 dL/dI U
-        g = plan.raster_bwd(p, plan.blasm_bwd(dUd.contiguous()))
+        dUd = plan.intensity_bwd(Ud, dI.to(torch.float32).contiguous())
+        g = plan.raster_bwd(p, plan.blasm_bwd(dUd))
         return (None, *[g[k] for k in PARAM_KEYS])
 
 

@@ -54,6 +54,7 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_plan_set_workspace", "cgh_plan_set_tuning", "cgh_plan_get_tuning",
            "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
+           "cgh_intensity", "cgh_intensity_bwd",
            "cgh_step", "cgh_step_scaled", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
            "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = True):
     lib.cgh_blasm_fwd.argtypes = [vp, vp, vp, vp]
     lib.cgh_blasm_bwd.argtypes = [vp, vp, vp, vp]
     lib.cgh_intensity_loss.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.cgh_intensity.argtypes = [vp, vp, vp, vp]
+    lib.cgh_intensity_bwd.argtypes = [vp, vp, vp, vp, vp]
     lib.cgh_forward_loss.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp]
     lib.cgh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads), vp]
     lib.cgh_step_scaled.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads),
@@ -411,6 +414,29 @@ class Plan:
                                        ctypes.c_void_p(_stream(stream))), "cgh_intensity_loss")
         return loss, dUd
 
+    def intensity(self, Ud, out=None, stream=None) -> torch.Tensor:
+        """cgh_intensity: I = |Ud|^2, float32 [L, C, H, W]."""
+        shape = (self.L, self.C, self.H, self.W)
+        _need(Ud, torch.complex64, shape, "Ud")
+        I = out if out is not None else torch.empty(shape, dtype=torch.float32, device=self.device)
+        _need(I, torch.float32, shape, "I_out")
+        _check(_lib.cgh_intensity(self._h, ctypes.c_void_p(Ud.data_ptr()),
+                                  ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(_stream(stream))),
+               "cgh_intensity")
+        return I
+
+    def intensity_bwd(self, Ud, dI, out=None, stream=None) -> torch.Tensor:
+        """cgh_intensity_bwd: dL/dUd = 2 dL/dI Ud, complex64 [L, C, H, W]."""
+        shape = (self.L, self.C, self.H, self.W)
+        _need(Ud, torch.complex64, shape, "Ud")
+        _need(dI, torch.float32, shape, "dI")
+        dUd = out if out is not None else torch.empty(shape, dtype=torch.complex64, device=self.device)
+        _need(dUd, torch.complex64, shape, "dUd_out")
+        _check(_lib.cgh_intensity_bwd(self._h, ctypes.c_void_p(Ud.data_ptr()),
+                                      ctypes.c_void_p(dI.data_ptr()), ctypes.c_void_p(dUd.data_ptr()),
+                                      ctypes.c_void_p(_stream(stream))), "cgh_intensity_bwd")
+        return dUd
+
     def forward_loss(self, params, target, loss_out=None, stream=None) -> torch.Tensor:
         prm = self._params(params)
         _need(target, torch.float32, (self.L, self.C, self.H, self.W), "target")
@@ -476,15 +502,30 @@ def raster_fwd_noalloc(params, H: int, W: int, cutoff: float = 1.0 / 255.0, out=
               "phase": (N, C), "alpha_raw": (N,)}
     for k in PARAM_KEYS:
         _need(params[k], torch.float32, shapes[k], k)
+    dev = params["theta"].device
+    check_same_device(dev, [(k, params[k].device) for k in PARAM_KEYS]
+                      + ([("U_out", out.device)] if out is not None else [])
+                      + ([("stream", stream.device)] if stream is not None else []))
     prm = _Params(N, *[ctypes.c_void_p(params[k].data_ptr()) for k in PARAM_KEYS])
-    U = out if out is not None else torch.empty(C, H, W, dtype=torch.complex64,
-                                                device=params["theta"].device)
+    U = out if out is not None else torch.empty(C, H, W, dtype=torch.complex64, device=dev)
     _need(U, torch.complex64, (C, H, W), "U_out")
-    _check(lib.cgh_raster_fwd_noalloc(int(H), int(W), C, float(cutoff), ctypes.byref(prm),
-                                      ctypes.c_void_p(U.data_ptr()),
-                                      ctypes.c_void_p(_stream(stream))),
-           "cgh_raster_fwd_noalloc")
+    # the entry point works on the current device: make it the parameters' device
+    with torch.cuda.device(dev):
+        _check(lib.cgh_raster_fwd_noalloc(int(H), int(W), C, float(cutoff), ctypes.byref(prm),
+                                          ctypes.c_void_p(U.data_ptr()),
+                                          ctypes.c_void_p(_stream(stream))),
+               "cgh_raster_fwd_noalloc")
     return U
+
+
+def check_same_device(device, named_devices) -> None:
+    """Raise CGHError unless every (name, torch.device) pair is on `device` (a device without
+    an index means the current one only when `device` has none either)."""
+    want = torch.device(device)
+    for name, d in named_devices:
+        d = torch.device(d)
+        if d.type != want.type or (d.index != want.index):
+            raise CGHError(f"{name} is on {d}, but the parameters are on {want}")
 
 
 def adam_step(groups, step: int, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

@@ -450,6 +450,24 @@ extern "C" cgh_status cgh_intensity_loss(cgh_plan* plan, const void* Ud, const f
   return CGH_OK;
 }
 
+extern "C" cgh_status cgh_intensity(cgh_plan* plan, const void* Ud, float* I_out, void* stream) {
+  CGH_CHECK(check_call(plan, nullptr));
+  if (!Ud || !I_out) return fail(CGH_ERR_ARG, "NULL argument");
+  const long long total = (long long)plan->L * plan->C * plan->H * plan->W;
+  CGH_TRY(launch_intensity(total, (const float2*)Ud, I_out, (cudaStream_t)stream), "cgh_intensity");
+  return CGH_OK;
+}
+
+extern "C" cgh_status cgh_intensity_bwd(cgh_plan* plan, const void* Ud, const float* dI,
+                                        void* dUd_out, void* stream) {
+  CGH_CHECK(check_call(plan, nullptr));
+  if (!Ud || !dI || !dUd_out) return fail(CGH_ERR_ARG, "NULL argument");
+  const long long total = (long long)plan->L * plan->C * plan->H * plan->W;
+  CGH_TRY(launch_intensity_bwd(total, (const float2*)Ud, dI, (float2*)dUd_out,
+                               (cudaStream_t)stream), "cgh_intensity_bwd");
+  return CGH_OK;
+}
+
 static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const float* target,
                                 float* loss_out, bool want_grad, cudaStream_t s,
                                 bool rebin = true) {

@@ -228,6 +228,26 @@ __global__ void k_loss_pointwise(const __grid_constant__ BlasmDev bl, long long 
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
+// Intensity of a complex field (Sec. 3.2: I = |U|^2), element-wise over `total` values.
+__global__ void k_intensity(long long total, const float2* __restrict__ U, float* __restrict__ I) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 u = __ldg(&U[i]);
+    I[i] = fmaf(u.x, u.x, u.y * u.y);
+  }
+}
+
+// Its adjoint: with dL/dI given, dL/dRe + j dL/dIm = 2 dL/dI (Re U + j Im U).
+__global__ void k_intensity_bwd(long long total, const float2* __restrict__ U,
+                                const float* __restrict__ dI, float2* __restrict__ dU) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 u = __ldg(&U[i]);
+    const float g = 2.0f * __ldg(&dI[i]);
+    dU[i] = make_float2(g * u.x, g * u.y);
+  }
+}
+
 // loss = sum(partials) / (L C H W), summed in FP64 in a fixed order.
 __global__ void k_loss_finalize(const float* __restrict__ partials, int count, double inv_norm,
                                 float* __restrict__ out) {
@@ -446,6 +466,28 @@ cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* ta
   prof_begin(KID_LOSS_POINTWISE, s);
   k_loss_pointwise<<<pointwise_loss_blocks(p), 256, 0, s>>>(p->bl, total, gscale, Ud, target,
                                                            partials, dUd);
+  prof_end(KID_LOSS_POINTWISE, s);
+  return cudaGetLastError();
+}
+
+static unsigned elementwise_blocks(long long total) {
+  long long b = (total + 255) / 256;
+  return (unsigned)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+cudaError_t launch_intensity(long long total, const float2* U, float* I, cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  prof_begin(KID_LOSS_POINTWISE, s);
+  k_intensity<<<elementwise_blocks(total), 256, 0, s>>>(total, U, I);
+  prof_end(KID_LOSS_POINTWISE, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_bwd(long long total, const float2* U, const float* dI, float2* dU,
+                                 cudaStream_t s) {
+  if (total <= 0) return cudaSuccess;
+  prof_begin(KID_LOSS_POINTWISE, s);
+  k_intensity_bwd<<<elementwise_blocks(total), 256, 0, s>>>(total, U, dI, dU);
   prof_end(KID_LOSS_POINTWISE, s);
   return cudaGetLastError();
 }

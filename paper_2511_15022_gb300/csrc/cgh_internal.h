@@ -143,6 +143,10 @@ cudaError_t launch_loss_finalize(cgh_plan* p, const float* partials, int count, 
 // sum(partials) * inv (FP64, fixed order) -> out[0]
 cudaError_t launch_loss_finalize_scaled(const float* partials, int count, double inv, float* out,
                                         cudaStream_t s);
+// I = |U|^2 and its adjoint dU = 2 dI U, element-wise over `total` complex values
+cudaError_t launch_intensity(long long total, const float2* U, float* I, cudaStream_t s);
+cudaError_t launch_intensity_bwd(long long total, const float2* U, const float* dI, float2* dU,
+                                 cudaStream_t s);
 int rows_loss_blocks(const cgh_plan* p);
 int pointwise_loss_blocks(const cgh_plan* p);
 // api.cu

@@ -29,6 +29,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "cgh_internal.h"
 
 namespace cgh {
@@ -621,12 +623,18 @@ static cudaError_t bin(cgh_plan* p, const cgh_params* prm, cudaStream_t s) {
   }
   prof_begin(KID_SCAN_TILES, s);
   const size_t stage_bytes = sizeof(int) * scan_stage_ints(T < kScanChunk ? T : kScanChunk);
-  static bool attr = false;  // opt in to more than 48 KB of dynamic shared memory once
-  if (!attr) {
+  // opt in to more than 48 KB of dynamic shared memory, once per device (the attribute
+  // belongs to the function on the current device)
+  constexpr int kMaxDev = 64;
+  static std::atomic<bool> attr[kMaxDev];
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev || !attr[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(k_scan_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(int) * scan_stage_ints(kScanChunk)));
     if (e != cudaSuccess) return e;
-    attr = true;
+    if (dev >= 0 && dev < kMaxDev) attr[dev].store(true, std::memory_order_release);
   }
   k_scan_tiles<<<1, 1024, stage_bytes, s>>>(T, p->pair_capacity, tile_count, tile_start, status);
   prof_end(KID_SCAN_TILES, s);

@@ -144,7 +144,7 @@ def planted_targets(count: int, H: int, W: int, wavelengths_m, pitch_m: float, z
     for i in range(count):
         p = {k: torch.from_numpy(v).to(device)
              for k, v in inputs.planted_scene(n_planted, C, H, W, seed + i).items()}
-        I = plan.blasm_fwd(plan.raster_fwd(p))[0].abs().square()
+        I = plan.intensity(plan.blasm_fwd(plan.raster_fwd(p)))[0]
         I.mul_(mean_intensity / float(I.mean().clamp_min(1e-12)))
         out[i] = I.clamp_(0.0, 1.0)
     plan.close()

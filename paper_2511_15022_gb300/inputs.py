@@ -98,13 +98,17 @@ def batched_64(seed: int = SEED_GAUSSIANS + 3, count: int = 64) -> List[Workload
     return out
 
 
+def _draw_means(rng, N: int, H: int, W: int):
+    """The first draws of a parameter set: Gaussian means uniform over [0, W] x [0, H]."""
+    return rng.uniform(0.0, W, size=N), rng.uniform(0.0, H, size=N)
+
+
 def gaussian_params(N: int, C: int, H: int, W: int, seed: int, s_min_px: float = 0.5,
                     s_max_px: float = 4.0, dtype=np.float32) -> dict:
     """Pre-activation Gaussian parameters, structure of arrays:
     xy_raw [N,2], s_raw [N,2], theta [N], amp [N,C], phase [N,C], alpha_raw [N]."""
     rng = np.random.default_rng(seed)
-    x = rng.uniform(0.0, W, size=N)
-    y = rng.uniform(0.0, H, size=N)
+    x, y = _draw_means(rng, N, H, W)
     lim = 1.0 - 1e-6
     xy_raw = np.stack([np.arctanh(np.clip(2.0 * x / W - 1.0, -lim, lim)),
                        np.arctanh(np.clip(2.0 * y / H - 1.0, -lim, lim))], axis=1)
@@ -166,9 +170,9 @@ def planted_scene(N: int, C: int, H: int, W: int, seed: int, blobs: int = 8,
     maximum 1) at the Gaussian's mean.  A random-phase scene would render as speckle; this
     one renders as an image-like intensity that the scene's own parameters reproduce."""
     p = gaussian_params(N, C, H, W, seed, dtype=np.float64)
+    # the same mean draws gaussian_params started from (same seed, same first draws)
+    x, y = _draw_means(np.random.default_rng(seed), N, H, W)
     rng = np.random.default_rng(seed ^ 0x5EED)
-    x = (np.tanh(p["xy_raw"][:, 0]) + 1.0) / 2.0 * W
-    y = (np.tanh(p["xy_raw"][:, 1]) + 1.0) / 2.0 * H
     amp = np.zeros((N, C))
     for c in range(C):
         for _ in range(blobs):

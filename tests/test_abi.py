@@ -55,3 +55,16 @@ def test_host_only_calls_without_gpu():
     assert lib.cgh_plan_create(7, 16, 1, 1, 2, lam, 8e-6, z, 0.0, 1 / 255, 10, ctypes.byref(h)) == 5
     assert lib.cgh_raster_fwd(None, None, None, None) == 1
     assert lib.cgh_adam_step(None, 0, 1, 0.9, 0.999, 1e-8, None) == 1
+
+
+def test_noalloc_binding_rejects_tensors_on_another_device():
+    """The allocation-free raster runs on the current device, which its binding makes the
+    parameters' device; an output or a stream on another device is refused before any call."""
+    import torch
+    from paper_2511_15022_gb300 import cgh
+    d0, d1 = torch.device("cuda", 0), torch.device("cuda", 1)
+    cgh.check_same_device(d0, [("U_out", d0), ("stream", torch.device("cuda", 0))])
+    with pytest.raises(cgh.CGHError, match="U_out is on cuda:1"):
+        cgh.check_same_device(d0, [("xy_raw", d0), ("U_out", d1)])
+    with pytest.raises(cgh.CGHError, match="stream"):
+        cgh.check_same_device(d1, [("stream", d0)])

@@ -1,0 +1,74 @@
+"""The Adam step inside the timed optimisation loop (cgh_adam_step, and the table form
+cgh_adam_step_table used by the batched optimiser) against the FP64 oracle's Adam, which is
+itself pinned to torch.optim.Adam on the CPU.  Six parameter groups with the paper's
+per-group learning rates (Sec. 4), five steps with a fresh gradient every step, so the bias
+corrections of steps 1..5 are all exercised.  Two sizes: the headline 200k-Gaussian RGB
+parameter set (every group a multiple of four elements: the 16-byte kernel) and a ragged
+1001-Gaussian set (the element-wise kernel)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_15022_gb300 import inputs
+from paper_2511_15022_gb300.optim import LRS
+from tests.gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 5
+STATE_TOL = 1e-6   # FP32 state against FP64: a few roundings per element
+DELTA_TOL = 1e-3   # parameter change p_t - p_0: FP32 rounding of p is ~1e-7 of |p| per step
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda", 0)
+
+
+def _run(N, C, dev, table: bool):
+    import torch
+    from paper_2511_15022_gb300 import cgh
+    from paper_2511_15022_gb300.cgh import PARAM_KEYS
+    p0 = inputs.gaussian_params(N, C, 64, 96, seed=N + 5)
+    rng = np.random.default_rng(N + 6)
+    grads = [{k: rng.standard_normal(p0[k].shape).astype(np.float32) for k in PARAM_KEYS}
+             for _ in range(STEPS)]
+    p = {k: torch.from_numpy(p0[k].copy()).to(dev) for k in PARAM_KEYS}
+    m = {k: torch.zeros_like(p[k]) for k in PARAM_KEYS}
+    v = {k: torch.zeros_like(p[k]) for k in PARAM_KEYS}
+    g = {k: torch.zeros_like(p[k]) for k in PARAM_KEYS}
+    tab = cgh.AdamTable([(p[k], m[k], v[k], g[k], LRS[k]) for k in PARAM_KEYS]) if table else None
+    # oracle state in FP64, started from the same FP32 values
+    rp = {k: p0[k].astype(np.float64).copy() for k in PARAM_KEYS}
+    rm = {k: np.zeros_like(rp[k]) for k in PARAM_KEYS}
+    rv = {k: np.zeros_like(rp[k]) for k in PARAM_KEYS}
+    for t in range(1, STEPS + 1):
+        for k in PARAM_KEYS:
+            g[k].copy_(torch.from_numpy(grads[t - 1][k]))
+        if table:
+            tab.step()
+        else:
+            cgh.adam_step([(p[k], g[k], m[k], v[k], LRS[k]) for k in PARAM_KEYS], t)
+        for k in PARAM_KEYS:
+            oracle.adam(rp[k], grads[t - 1][k], rm[k], rv[k], LRS[k], t)
+    torch.cuda.synchronize()
+    for k in PARAM_KEYS:
+        gp = p[k].double().cpu().numpy()
+        assert rel_l2(m[k].double().cpu().numpy(), rm[k]) < STATE_TOL, ("exp_avg", k)
+        assert rel_l2(v[k].double().cpu().numpy(), rv[k]) < STATE_TOL, ("exp_avg_sq", k)
+        assert rel_l2(gp, rp[k]) < STATE_TOL, ("param", k)
+        d0 = p0[k].astype(np.float64)
+        assert rel_l2(gp - d0, rp[k] - d0) < DELTA_TOL, ("update", k)
+
+
+@pytest.mark.parametrize("N", [200_000, 1001])
+def test_adam_step_matches_oracle(N, dev):
+    _run(N, 3, dev, table=False)
+
+
+@pytest.mark.parametrize("N", [200_000, 1001])
+def test_adam_table_matches_oracle(N, dev):
+    _run(N, 3, dev, table=True)

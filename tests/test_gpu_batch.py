@@ -1,10 +1,15 @@
-"""Batched holograms in one CUDA graph, the block-shape autotuner and the table Adam,
-each against the single-hologram entry points (themselves checked against the oracle)."""
+"""Batched holograms in one CUDA graph, the block-shape autotuner and the table Adam:
+every hologram of a batch against the FP64 oracle's step directly, and the batch against the
+single-hologram entry points."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2511_15022_gb300 import inputs
-from tests.gpu_util import rel_l2, to_dev
+from tests.gpu_util import rel_l2, to64, to_dev
+
+LOSS_TOL = 1e-4
+GRAD_TOL = 1e-3
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +57,36 @@ def test_batch_graph_and_sequential_match_single_steps(dev):
             for k in g:
                 assert rel_l2(g[k].cpu().numpy(), ref_g[k].cpu().numpy()) < 1e-4, k
     assert batch.kernels_per_step > 3 * 10
+
+
+def test_batch_matches_oracle_per_hologram(dev):
+    """Each hologram of a mixed batch (sizes, channel and plane counts differ; one plane at
+    z = 0) after a graph replay, against the oracle's forward + backward of that hologram."""
+    import torch
+    from paper_2511_15022_gb300 import cgh
+    ws = [inputs.custom(64, 96, 400, wavelengths_m=(638e-9, 520e-9, 450e-9), z_m=(0.0, 5e-3), seed=84),
+          inputs.custom(128, 128, 1500, seed=85),
+          inputs.custom(100, 120, 900, wavelengths_m=(520e-9,), z_m=(3e-3, 6e-3, 9e-3), seed=86),
+          inputs.custom(96, 160, 1200, wavelengths_m=(638e-9, 450e-9), z_m=(0.0, 4e-3, 8e-3), seed=87)]
+    plans = [_plan(w, dev) for w in ws]
+    batch = cgh.Batch(plans)
+    data = []
+    for i, (w, plan) in enumerate(zip(ws, plans)):
+        p_np = inputs.params_for(w)
+        t_np = inputs.blob_targets(w.L, w.C, w.H, w.W, seed=95 + i)
+        g = plan.empty_grads(w.N)
+        loss = torch.empty(1, device=dev)
+        batch.bind(i, to_dev(p_np, dev), torch.from_numpy(t_np).to(dev), g, loss)
+        data.append((w, p_np, t_np, loss, g))
+    batch.step(use_graph=True)
+    batch.step(use_graph=True)  # a replay of the captured graph
+    torch.cuda.synchronize()
+    for w, p_np, t_np, loss, g in data:
+        ref = oracle.step(to64(p_np), t_np.astype(np.float64), w.H, w.W, w.wavelengths_m,
+                          w.pitch_m, w.z_m, cutoff=w.cutoff)
+        assert abs(loss.item() - ref["loss"]) <= LOSS_TOL * abs(ref["loss"]), w.name
+        for k in g:
+            assert rel_l2(g[k].double().cpu().numpy(), ref["grads"][k]) < GRAD_TOL, (w.name, k)
 
 
 def test_autotune_keeps_a_valid_fastest_shape(dev):

@@ -80,3 +80,33 @@ def test_fused_step_equals_composition(setup):
         assert rel_l2(g[k].double().cpu().numpy(), g2[k].double().cpu().numpy()) < 1e-4, k
     st = plan.status()
     assert not st["overflow"] and not st["nonfinite"]
+
+
+def test_blasm_fwd_one_channel_all_planes(setup):
+    """Full-size propagation of the 638 nm channel to all three planes (0, 5 and 10 mm) in
+    the kernels the benchmark times, against the oracle."""
+    import torch
+    w, p, plan, dev = setup
+    U0 = inputs.random_field(w.C, w.H, w.W, seed=66)
+    Ud = plan.blasm_fwd(torch.from_numpy(U0).to(dev))
+    c = 0
+    ref = oracle.blasm_fwd(U0[c:c + 1], [w.wavelengths_m[c]], w.pitch_m, list(w.z_m), w.pad)
+    for l in range(w.L):
+        assert rel_l2(c64(Ud[l, c]), ref[l, 0]) < FIELD_TOL, l
+
+
+def test_blasm_bwd_one_channel_all_planes(setup):
+    """Adjoint propagation (Suppl. BLASM backward: conj(H) under the same band limit, summed
+    over the planes) at full size in the kernels the benchmark times: dL/dUd non-zero in one
+    channel only, so the oracle needs only that channel; the other channels must stay zero."""
+    import torch
+    w, p, plan, dev = setup
+    c = 1
+    dUd = np.zeros((w.L, w.C, w.H, w.W), np.complex64)
+    dUd[:, c] = inputs.random_field(w.L, w.H, w.W, seed=65)
+    dU0 = c64(plan.blasm_bwd(torch.from_numpy(dUd).to(dev)))
+    ref = oracle.blasm_bwd(dUd[:, c:c + 1], [w.wavelengths_m[c]], w.pitch_m, list(w.z_m), w.pad)
+    assert rel_l2(dU0[c], ref[0]) < FIELD_TOL
+    for other in range(w.C):
+        if other != c:
+            assert np.abs(dU0[other]).max() == 0.0, other

@@ -45,6 +45,22 @@ def test_noalloc_matches_planned_raster_on_two_calls(dev):
         assert rel_l2(c64(out), ref) < FIELD_TOL
 
 
+def test_noalloc_at_its_tile_limit(dev):
+    """2048 x 2048 pixels, the largest grid the fixed array takes (16384 tiles: the tile scan
+    then needs more than 48 KB of shared memory), on two calls in a row."""
+    import torch
+    from paper_2511_15022_gb300 import cgh
+    w = inputs.custom(2048, 2048, 40000, wavelengths_m=(638e-9, 520e-9), z_m=(0.0,), seed=73)
+    p = to_dev(inputs.params_for(w), dev)
+    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
+                    max_gaussians=w.N, device=dev)
+    ref = c64(plan.raster_fwd(p))
+    for _ in range(2):
+        U = cgh.raster_fwd_noalloc(p, w.H, w.W, w.cutoff)
+        torch.cuda.synchronize()
+        assert rel_l2(c64(U), ref) < FIELD_TOL
+
+
 def test_noalloc_refuses_inputs_beyond_its_scratch(dev):
     import torch
     from paper_2511_15022_gb300 import cgh
