@@ -17,6 +17,12 @@ pytestmark = pytest.mark.gpu
 
 STEPS = 5
 STATE_TOL = 1e-6   # FP32 state against FP64: a few roundings per element
+
+# The C ABI takes the hyper-parameters as FP32, so the oracle is given the same values: beta2
+# = 0.999 rounds to 0.99900001287 in FP32, which makes 1 - beta2 differ from 1e-3 by 1.3e-5
+# relative -- the same update, evaluated with the rates the kernel is actually given.
+F32 = lambda x: float(np.float32(x))  # noqa: E731
+BETA1, BETA2, EPS = F32(0.9), F32(0.999), F32(1e-8)
 DELTA_TOL = 1e-3   # parameter change p_t - p_0: FP32 rounding of p is ~1e-7 of |p| per step
 
 
@@ -53,7 +59,7 @@ def _run(N, C, dev, table: bool):
         else:
             cgh.adam_step([(p[k], g[k], m[k], v[k], LRS[k]) for k in PARAM_KEYS], t)
         for k in PARAM_KEYS:
-            oracle.adam(rp[k], grads[t - 1][k], rm[k], rv[k], LRS[k], t)
+            oracle.adam(rp[k], grads[t - 1][k], rm[k], rv[k], F32(LRS[k]), t, BETA1, BETA2, EPS)
     torch.cuda.synchronize()
     for k in PARAM_KEYS:
         gp = p[k].double().cpu().numpy()
