@@ -32,21 +32,27 @@ UNIT = "it/s"
 from paper_2511_15022_gb300.optim import LRS  # noqa: E402  (Adam rates per group, Sec. 4)
 
 
-def algorithmic_bytes(w) -> dict:
+def algorithmic_bytes(w, ident: int = 0) -> dict:
     """Compulsory HBM bytes per launch of each FFT-pass kernel: complex64 units of
-    S = H*W*8 bytes per channel (pad / crop halves skipped, planes fused).  rows_loss is the
-    fused pass with the gradient; the forward-only launch moves 2.5 units instead of 4.5."""
+    S = H*W*8 bytes per channel (pad / crop halves skipped, planes fused).  `ident` planes
+    propagate by the identity (distance 0) and are taken in the pixel domain: they move no
+    column or loss-row bytes; their loss pass reads U(0) and their targets and writes the
+    seed, and the last row pass adds that seed (one more read).  rows_loss is the fused pass
+    with the gradient; the forward-only launch moves 2.5 units per plane instead of 4.5."""
     S = w.H * w.W * 8
-    C, L = w.C, w.L
-    return {
+    C, Lp = w.C, w.L - ident
+    out = {
         "k_rows_pad_fwd": (1 + 2) * C * S,
-        "k_cols_fwd_planes": (2 + 2 * L) * C * S,
-        "k_rows_loss": (2 + 0.5 + 2) * L * C * S,
-        "k_cols_bwd_planes": (2 * L + 2) * C * S,
-        "k_rows_inv_crop": (2 + 1) * C * S,
+        "k_cols_fwd_planes": (2 + 2 * Lp) * C * S,
+        "k_rows_loss": (2 + 0.5 + 2) * Lp * C * S,
+        "k_cols_bwd_planes": (2 * Lp + 2) * C * S,
+        "k_rows_inv_crop": (2 + 1 + (1 if ident else 0)) * C * S,
         "k_raster_fwd": 1 * C * S,
         "k_raster_bwd": 1 * C * S,
     }
+    if ident:
+        out["k_ident_loss"] = (2 + 0.5 * ident) * C * S
+    return out
 
 
 def raster_pairs(p: dict, cutoff: float) -> float:
@@ -66,39 +72,56 @@ def raster_pairs(p: dict, cutoff: float) -> float:
     return float(np.sum(np.pi * m * np.sqrt(np.maximum(det, 0.0))))
 
 
-def step_work(w, mode: str, pairs: float) -> dict:
+def step_work(w, mode: str, pairs: float, ident: int = 0) -> dict:
     """Algorithmic work of one optimisation step per kernel: HBM bytes, FP32 flops (FFT
     5 n log2 n per length-n transform plus 6 per transfer-function multiply; raster 15 per
     pair forward, 45 backward) and MUFU operations (2 per transfer-function bin and plane,
     1 exponential per raster pair).  mode 'autograd' runs a forward-only pass (raster, rows,
-    columns, loss rows without gradient) before the fused step."""
+    columns, loss rows without gradient) before the fused step.  `ident` planes propagate by
+    the identity and need no transform: the column and loss-row passes count only the other
+    Lp = L - ident planes, and the identity planes' pixel-domain loss pass is added."""
     import math
     H, W, C, L = w.H, w.W, w.C, w.L
+    Lp = L - ident
     Ny, Nx = w.pad * H, w.pad * W
     S = H * W * 8
     fx = 5.0 * Nx * math.log2(Nx)   # one row transform
     fy = 5.0 * Ny * math.log2(Ny)   # one column transform
-    bins = C * L * Ny * Nx
+    bins = C * Lp * Ny * Nx
     fwd_pass = 2 if mode == "autograd" else 1
     N = w.N
     work = {
         "k_rows_pad_fwd": (3 * C * S, C * H * fx, 0.0, fwd_pass),
-        "k_cols_fwd_planes": ((2 + 2 * L) * C * S, C * Nx * (1 + L) * fy + 6.0 * bins, 2.0 * bins,
-                              fwd_pass),
-        "k_cols_bwd_planes": ((2 * L + 2) * C * S, C * Nx * (L + 1) * fy + 6.0 * bins, 2.0 * bins, 1),
-        "k_rows_inv_crop": (3 * C * S, C * H * fx, 0.0, 1),
+        "k_cols_fwd_planes": ((2 + 2 * Lp) * C * S, C * Nx * (1 + Lp) * fy + 6.0 * bins,
+                              2.0 * bins, fwd_pass),
+        "k_cols_bwd_planes": ((2 * Lp + 2) * C * S, C * Nx * (Lp + 1) * fy + 6.0 * bins,
+                              2.0 * bins, 1),
+        "k_rows_inv_crop": ((3 + (1 if ident else 0)) * C * S, C * H * fx, 0.0, 1),
         "k_raster_fwd": (C * S + 48.0 * N, 15.0 * pairs, pairs, fwd_pass),
         "k_raster_bwd": (C * S + 96.0 * N, 45.0 * pairs, pairs, 1),
         "k_adam": (7 * 4.0 * (6 + 2 * C) * N, 0.0, 0.0, 1),
     }
+    if Lp == 0:
+        for k in ("k_rows_pad_fwd", "k_cols_fwd_planes", "k_cols_bwd_planes", "k_rows_inv_crop"):
+            del work[k]
     # amounts per step: kernels of the forward-only pass run twice in autograd mode
     work = {k: (b * n, f * n, u * n, n) for k, (b, f, u, n) in work.items()}
-    grad_rows = (4.5 * L * C * S, L * C * H * 2 * fx, 0.0)
-    if mode == "autograd":  # one forward-only launch + one with the gradient
-        nograd = (2.5 * L * C * S, L * C * H * fx, 0.0)
-        work["k_rows_loss"] = tuple(a + b for a, b in zip(nograd, grad_rows)) + (2,)
-    else:
-        work["k_rows_loss"] = grad_rows + (1,)
+    if Lp > 0:
+        grad_rows = (4.5 * Lp * C * S, Lp * C * H * 2 * fx, 0.0)
+        if mode == "autograd":  # one forward-only launch + one with the gradient
+            nograd = (2.5 * Lp * C * S, Lp * C * H * fx, 0.0)
+            work["k_rows_loss"] = tuple(a + b for a, b in zip(nograd, grad_rows)) + (2,)
+        else:
+            work["k_rows_loss"] = grad_rows + (1,)
+    if ident:
+        # reads U(0) and the identity planes' targets; the launch with the gradient also
+        # writes the seed
+        grad_id = ((2 + 0.5 * ident) * C * S, 6.0 * ident * C * H * W, 0.0)
+        if mode == "autograd":
+            nograd_id = ((1 + 0.5 * ident) * C * S, 4.0 * ident * C * H * W, 0.0)
+            work["k_ident_loss"] = tuple(a + b for a, b in zip(nograd_id, grad_id)) + (2,)
+        else:
+            work["k_ident_loss"] = grad_id + (1,)
     return work
 
 
@@ -1221,6 +1244,26 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
+    # ---- context: the same steps with every plane propagated through the FFT passes (the
+    # plane at 0 mm too), i.e. without the pixel-domain path for identity planes
+    full_prop = None
+    if plan.identity_planes and plan.get_tuning()["identity_planes"] == 1:
+        plan.set_tuning(identity_planes=2)
+        k_full = min(args.steps, 200)
+        for _ in range(3):
+            step(target)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(k_full):
+            step(target)
+        f1.record(stream)
+        barrier()
+        plan.set_tuning(identity_planes=1)
+        fms = f0.elapsed_time(f1) / k_full
+        full_prop = {"ms_per_step": fms, "it_per_s": 1000.0 / fms, "steps": k_full,
+                     "what": "identity_planes = 2: the 0 mm plane propagated by FFT too"}
+
     ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], device=dev)
     value = aggregate_throughput(args.steps, world, ms_total)
     e2e_value = aggregate_throughput(args.steps, world, e2e_ms)
@@ -1232,7 +1275,8 @@ def main():
         # FP32 peak from the unit counts and the sampled clock: SMs x 128 FP32 lanes x 2 flops
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_nominal = sms * 128 * 2 * sm_mhz * 1e6
-        work = step_work(w, args.mode, raster_pairs(params_np, w.cutoff))
+        ident = len(plan.identity_planes) if plan.get_tuning()["identity_planes"] == 1 else 0
+        work = step_work(w, args.mode, raster_pairs(params_np, w.cutoff), ident)
         roof = rooflines(work, prof, args.steps, peak, fp32_nominal, alu["sfu_ops_per_s"])
         per_kernel = {k: {"ms_per_launch": v["ms"] / v["launches"], "launches": v["launches"],
                           "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
@@ -1281,7 +1325,8 @@ def main():
                        "z_mm": [z * 1e3 for z in w.z_m], "pad": w.pad, "mode": args.mode,
                        "optimizer": "Adam (per-group lr)", "parallelism": f"replicas x{world}",
                        "l2": "working set ~0.5 GB > 129 MB L2 (inputs larger than L2)",
-                       "tuning": plan.get_tuning()},
+                       "tuning": plan.get_tuning(),
+                       "identity_planes": list(plan.identity_planes)},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
@@ -1294,6 +1339,7 @@ def main():
                                                  for k, v in params.items()}, w.cutoff)},
             "torch_cufft_blasm": torch_blasm_ms(w, dev) if not args.no_extras else None,
             "autotuned": tuned is not None,
+            "every_plane_propagated": full_prop,
         }
         if not args.no_extras and world == 1:
             line["batched"] = batched_bench(dev, steps=min(50, max(5, args.steps // 4)), warmup=3)

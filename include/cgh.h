@@ -111,13 +111,22 @@ cgh_status cgh_plan_set_workspace(cgh_plan* plan, void* workspace, size_t bytes)
  *   fft_threads  threads per CTA of the FFT passes (128..1024)
  *   pair_capacity_per_gaussian  (Gaussian, tile) list capacity as a multiple of N
  *   fft_kernels  1: compile-time specialised FFT kernels where one matches the padded
- *                length and block shape (default), 2: generic mixed-radix kernels only */
+ *                length and block shape (default), 2: generic mixed-radix kernels only
+ *   identity_planes  1 (default): in cgh_forward_loss, cgh_step, cgh_step_scaled and the batch
+ *                step, planes whose propagation is the identity -- distance exactly 0, no
+ *                aperture, every frequency bin inside the band, so H = 1 in Algorithm 3 and
+ *                U(d) = U(0) -- take their loss and gradient seed on U(0) in the pixel domain
+ *                and skip the FFT passes; 2: propagate every plane through the FFT passes.
+ *                Both compute the same loss and gradients (the first without the FFT
+ *                round-off of an identity transform).  cgh_blasm_fwd/bwd always propagate
+ *                every plane. */
 typedef struct {
   int32_t col_block;
   int32_t row_block;
   int32_t fft_threads;
   int32_t pair_capacity_per_gaussian;
   int32_t fft_kernels;
+  int32_t identity_planes;
 } cgh_tuning;
 
 cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* tuning);
@@ -127,6 +136,13 @@ cgh_status cgh_plan_get_tuning(const cgh_plan* plan, cgh_tuning* out);
  * largest |signed frequency index| that passes |f_x| < f_x^max (resp. y), index c*L + l.
  * Computed on the host in FP64 exactly as the definition reads. */
 cgh_status cgh_plan_band_limits(const cgh_plan* plan, int32_t* kx_max, int32_t* ky_max);
+
+/* Planes whose propagation is the identity (host output, bit l set for plane l): distance
+ * exactly 0, no aperture and every frequency bin of every channel inside the band of
+ * Algorithm 3 (at d = 0 the phase k_z d vanishes and f_max = 1/lambda exceeds the grid's
+ * Nyquist frequency whenever lambda < 2 pitch, so H = 1).  With the tuning knob
+ * identity_planes = 1 the fused entry points take these planes in the pixel domain. */
+cgh_status cgh_plan_identity_planes(const cgh_plan* plan, uint32_t* mask_out);
 
 /* Loss taken by cgh_intensity_loss, cgh_forward_loss, cgh_step and the batch step of this
  * plan (Sec. 3.2).  kind = CGH_LOSS_MSE (default): L_MSE = 1/L sum_l mean_{c,p}

@@ -34,7 +34,7 @@ class _Grads(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("col_block", ctypes.c_int32), ("row_block", ctypes.c_int32),
                 ("fft_threads", ctypes.c_int32), ("pair_capacity_per_gaussian", ctypes.c_int32),
-                ("fft_kernels", ctypes.c_int32)]
+                ("fft_kernels", ctypes.c_int32), ("identity_planes", ctypes.c_int32)]
 
 
 class _AdanGroup(ctypes.Structure):
@@ -54,7 +54,7 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_plan_set_workspace", "cgh_plan_set_tuning", "cgh_plan_get_tuning",
            "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
-           "cgh_intensity", "cgh_intensity_bwd",
+           "cgh_intensity", "cgh_intensity_bwd", "cgh_plan_identity_planes",
            "cgh_step", "cgh_step_scaled", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
            "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_blasm_bwd.argtypes = [vp, vp, vp, vp]
     lib.cgh_intensity_loss.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.cgh_intensity.argtypes = [vp, vp, vp, vp]
+    lib.cgh_plan_identity_planes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
     lib.cgh_intensity_bwd.argtypes = [vp, vp, vp, vp, vp]
     lib.cgh_forward_loss.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, vp]
     lib.cgh_step.argtypes = [vp, ctypes.POINTER(_Params), vp, vp, ctypes.POINTER(_Grads), vp]
@@ -248,8 +249,9 @@ class Plan:
         return int(n.value)
 
     def set_tuning(self, col_block=0, row_block=0, fft_threads=0, pair_capacity_per_gaussian=0,
-                   fft_kernels=0):
-        t = _Tuning(col_block, row_block, fft_threads, pair_capacity_per_gaussian, fft_kernels)
+                   fft_kernels=0, identity_planes=0):
+        t = _Tuning(col_block, row_block, fft_threads, pair_capacity_per_gaussian, fft_kernels,
+                    identity_planes)
         with torch.cuda.device(self.device):
             _check(_lib.cgh_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
         if self._ws is not None:
@@ -309,6 +311,13 @@ class Plan:
         self._mask = mask  # the plan reads it at every later call
         _check(_lib.cgh_plan_set_loss(self._h, k, ctypes.c_void_p(mask.data_ptr()) if mask is not None
                                       else ctypes.c_void_p(0)), "cgh_plan_set_loss")
+
+    @property
+    def identity_planes(self) -> tuple:
+        """Indices of the planes whose propagation is the identity (cgh_plan_identity_planes)."""
+        m = ctypes.c_uint32()
+        _check(_lib.cgh_plan_identity_planes(self._h, ctypes.byref(m)), "cgh_plan_identity_planes")
+        return tuple(l for l in range(self.L) if (m.value >> l) & 1)
 
     def get_tuning(self) -> dict:
         t = _Tuning()

@@ -155,7 +155,8 @@ extern "C" cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L
   }
   BlasmDev& bl = p->bl;
   memset(&bl, 0, sizeof(bl));
-  bl.H = H; bl.W = W; bl.C = C; bl.L = L;
+  bl.H = H; bl.W = W; bl.C = C; bl.L = L; bl.Ltot = L;
+  for (int l = 0; l < L; ++l) bl.plane[l] = l;
   bl.Ny = (int)Ny; bl.Nx = (int)Nx;
   bl.oy = (int)((Ny - H) / 2); bl.ox = (int)((Nx - W) / 2);
   bl.inv_ntot = (float)(1.0 / ((double)Ny * (double)Nx));
@@ -194,6 +195,27 @@ extern "C" cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L
       t.ay = (float)(D * qy);
     }
   }
+  // Planes whose propagation is the identity: distance exactly 0 and no aperture, with every
+  // frequency bin of every channel inside the band (Algorithm 3 at d = 0: the phase k_z d is
+  // 0 and f_max = 1/lambda, so H = 1 on the whole grid and U(d) = crop(IFFT(FFT(pad U))) = U).
+  p->n_ident = 0;
+  p->ident_mask = 0u;
+  p->use_ident = 1;
+  p->bl_prop = bl;
+  p->bl_prop.L = 0;
+  for (int l = 0; l < L; ++l) {
+    bool ident = p->z[l] == 0.0 && aperture == 0.0;
+    for (int c = 0; c < C && ident; ++c) {
+      const TFConst& t = bl.tf[c * L + l];
+      ident = t.kx_max >= (int)(Nx / 2) && t.ky_max >= (int)(Ny / 2);
+    }
+    if (ident) {
+      p->ident_mask |= 1u << l;
+      ++p->n_ident;
+    } else {
+      p->bl_prop.plane[p->bl_prop.L++] = l;
+    }
+  }
   // twiddle tables tw[m] = exp(-2 pi i m / n), FP64 on the host
   const size_t tbytes = sizeof(float2) * (size_t)(Nx + Ny);
   float2* host_tw = (float2*)malloc(tbytes);
@@ -224,7 +246,8 @@ extern "C" cgh_status cgh_plan_create(int32_t H, int32_t W, int32_t C, int32_t L
     static const int rbs[] = {4, 2, 1, 8};
     bool done = false;
     for (int cb : cbs) {
-      if (done || Nx % cb || !spec_cols(0, (int)Ny, cb, nullptr, nullptr, nullptr, 0, nullptr, true))
+      if (done || Nx % cb ||
+          !spec_cols(0, (int)Ny, cb, nullptr, nullptr, nullptr, nullptr, 0, nullptr, true))
         continue;
       for (int rb : rbs) {
         if (spec_rows(0, (int)Nx, rb, cb, nullptr, nullptr, 0, nullptr, true)) {
@@ -304,6 +327,11 @@ extern "C" cgh_status cgh_plan_set_tuning(cgh_plan* plan, const cgh_tuning* t) {
     if (t->fft_kernels != 1 && t->fft_kernels != 2) return fail(CGH_ERR_ARG, "fft_kernels must be 1 or 2");
     plan->use_spec = t->fft_kernels == 1;
   }
+  if (t->identity_planes) {
+    if (t->identity_planes != 1 && t->identity_planes != 2)
+      return fail(CGH_ERR_ARG, "identity_planes must be 1 or 2");
+    plan->use_ident = t->identity_planes == 1;
+  }
   if (t->pair_capacity_per_gaussian) {
     if (t->pair_capacity_per_gaussian < 1) return fail(CGH_ERR_ARG, "pair capacity must be >= 1");
     plan->pair_cap_mult = t->pair_capacity_per_gaussian;
@@ -330,6 +358,7 @@ extern "C" cgh_status cgh_plan_get_tuning(const cgh_plan* plan, cgh_tuning* out)
   out->fft_threads = plan->fft_threads;
   out->pair_capacity_per_gaussian = plan->pair_cap_mult;
   out->fft_kernels = plan->use_spec ? 1 : 2;
+  out->identity_planes = plan->use_ident ? 1 : 2;
   return CGH_OK;
 }
 
@@ -343,12 +372,20 @@ extern "C" cgh_status cgh_plan_band_limits(const cgh_plan* plan, int32_t* kx_max
   return CGH_OK;
 }
 
+extern "C" cgh_status cgh_plan_identity_planes(const cgh_plan* plan, uint32_t* mask_out) {
+  if (!plan || !mask_out) return fail(CGH_ERR_ARG, "NULL argument");
+  *mask_out = plan->ident_mask;
+  return CGH_OK;
+}
+
 extern "C" cgh_status cgh_plan_set_loss(cgh_plan* plan, int32_t kind, const uint8_t* recon_mask) {
   if (!plan) return fail(CGH_ERR_ARG, "plan is NULL");
   if (kind != CGH_LOSS_MSE && kind != CGH_LOSS_RECON) return fail(CGH_ERR_ARG, "unknown loss kind");
   if (kind == CGH_LOSS_MSE && recon_mask) return fail(CGH_ERR_ARG, "a depth mask needs CGH_LOSS_RECON");
   plan->bl.loss_kind = kind;
   plan->bl.recon_mask = recon_mask;
+  plan->bl_prop.loss_kind = kind;  // the plane map of the fused step carries the same loss
+  plan->bl_prop.recon_mask = recon_mask;
   return CGH_OK;
 }
 
@@ -468,6 +505,11 @@ extern "C" cgh_status cgh_intensity_bwd(cgh_plan* plan, const void* Ud, const fl
   return CGH_OK;
 }
 
+// Planes whose propagation is the identity are handled in the pixel domain when the plan
+// allows it: their loss and gradient seed come from U(0) directly (k_ident_loss), and only the
+// other planes go through the column and loss row passes.
+static bool ident_path(const cgh_plan* p) { return p->use_ident && p->n_ident > 0; }
+
 static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const float* target,
                                 float* loss_out, bool want_grad, cudaStream_t s,
                                 bool rebin = true) {
@@ -476,9 +518,20 @@ static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const 
   float2* V = (float2*)(plan->ws + plan->off_V);
   float* partials = (float*)(plan->ws + plan->off_loss);
   CGH_TRY(launch_raster_fwd(plan, params, U0, s, rebin), "raster_fwd");
-  CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
-  CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s), "cols_fwd_planes");
-  CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad, loss_out), "rows_loss");
+  if (!ident_path(plan)) {
+    CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
+    CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s), "cols_fwd_planes");
+    CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad, loss_out), "rows_loss");
+    return CGH_OK;
+  }
+  const BlasmDev* prop = &plan->bl_prop;
+  if (prop->L > 0) CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
+  // after the row pass has read U(0): the identity planes' seed replaces it in place
+  const int own = rows_loss_blocks(plan, prop);
+  CGH_TRY(launch_ident_loss(plan, U0, target, partials + own, want_grad, s), "ident_loss");
+  CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s, prop), "cols_fwd_planes");
+  CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad, loss_out, prop,
+                           ident_loss_blocks(plan)), "rows_loss");
   return CGH_OK;
 }
 
@@ -499,8 +552,14 @@ static cgh_status step_impl(cgh_plan* plan, const cgh_params* params, const floa
   float2* U0 = (float2*)(plan->ws + plan->off_U0);  // reused for dL/dU(0)
   float2* Y = (float2*)(plan->ws + plan->off_Y);    // reused for the backward half grid
   float2* V = (float2*)(plan->ws + plan->off_V);
-  CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s), "cols_bwd_planes");
-  CGH_TRY(launch_rows_inv_crop(plan, Y, U0, plan->C, s), "rows_inv_crop");
+  if (!ident_path(plan)) {
+    CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s), "cols_bwd_planes");
+    CGH_TRY(launch_rows_inv_crop(plan, Y, U0, plan->C, s), "rows_inv_crop");
+  } else if (plan->bl_prop.L > 0) {
+    // dL/dU(0) = identity planes' seed (already in U0) + adjoint of the propagated planes
+    CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s, &plan->bl_prop), "cols_bwd_planes");
+    CGH_TRY(launch_rows_inv_crop(plan, Y, U0, plan->C, s, true), "rows_inv_crop");
+  }
   // the forward's binning is still valid for these parameters: reuse it
   CGH_TRY(launch_raster_bwd(plan, params, U0, grads, s, false, grad_scale), "raster_bwd");
   return CGH_OK;

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(512, 1) k_cols_fwd_planes(const __grid_constan
   __syncthreads();
   block_fft<false, MAXB>(S, bs, CB, fy);
   for (int l = 0; l < bl.L; ++l) {
-    const int cl = c * bl.L + l;
+    const int cl = c * bl.Ltot + bl.plane[l];
     for (int idx = threadIdx.x; idx < CB * Ny; idx += blockDim.x) {
       const int b = idx / Ny, i = idx - b * Ny;
       const int sx = signed_index(kb * CB + b, Nx), sy = signed_index(i, Ny);
@@ -97,7 +97,7 @@ template <int MAXB>
 __global__ void __launch_bounds__(512, 1) k_rows_inv_crop(const __grid_constant__ BlasmDev bl,
                                                         const FFTDesc fx, int RB, int CB, int bs,
                                                         const float2* __restrict__ half,
-                                                        float2* __restrict__ out) {
+                                                        float2* __restrict__ out, int accum) {
   extern __shared__ float2 sm[];
   const int batch = blockIdx.y;
   const int y0 = blockIdx.x * RB;
@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(512, 1) k_rows_inv_crop(const __grid_constant_
   float2* dst = out + (size_t)batch * H * W;
   for (int idx = threadIdx.x; idx < rows * W; idx += blockDim.x) {
     const int b = idx / W, x = idx - b * W;
-    dst[(size_t)(y0 + b) * W + x] = sm[b * bs + sidx(bl.ox + x)];
+    const float2 v = sm[b * bs + sidx(bl.ox + x)];
+    float2* o = &dst[(size_t)(y0 + b) * W + x];
+    *o = accum ? cadd(*o, v) : v;
   }
 }
 
@@ -126,7 +128,8 @@ __global__ void __launch_bounds__(512, 1) k_rows_loss(const __grid_constant__ Bl
                                                     float* __restrict__ partials, int want_grad) {
   extern __shared__ float2 sm[];
   __shared__ float red[32];
-  const int batch = blockIdx.y;  // l * C + c
+  const int batch = blockIdx.y;  // l * C + c (kernel planes)
+  const int plane = bl.plane[batch / bl.C];  // the hologram plane: target, mask
   const int y0 = blockIdx.x * RB;
   const int rows = min(RB, bl.H - y0);
   const int Nx = bl.Nx, W = bl.W, H = bl.H;
@@ -138,8 +141,8 @@ __global__ void __launch_bounds__(512, 1) k_rows_loss(const __grid_constant__ Bl
   }
   __syncthreads();
   block_fft<true, MAXB>(sm, bs, rows, fx);
-  const float gscale = 4.0f / ((float)bl.L * (float)bl.C * (float)H * (float)W);
-  const float* tg = target + (size_t)batch * H * W;
+  const float gscale = 4.0f / ((float)bl.Ltot * (float)bl.C * (float)H * (float)W);
+  const float* tg = target + ((size_t)plane * bl.C + batch % bl.C) * H * W;
   float acc = 0.f;
   for (int idx = threadIdx.x; idx < rows * Nx; idx += blockDim.x) {
     const int b = idx / Nx, k = idx - b * Nx;
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_loss(const __grid_constant__ Bl
       const float I = fmaf(u.x, u.x, u.y * u.y);
       const float t = tg[(size_t)(y0 + b) * W + x];
       const float d = I - t;
-      const float wd = loss_weight(bl, batch / bl.C, y0 + b, x, t) * d;
+      const float wd = loss_weight(bl, plane, y0 + b, x, t) * d;
       acc = fmaf(wd, d, acc);
       g = cscale(u, gscale * wd);
     }
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(512, 1) k_cols_bwd_planes(const __grid_constan
     }
     __syncthreads();
     block_fft<false, MAXB>(Wk, bs, CB, fy);
-    const int cl = c * bl.L + l;
+    const int cl = c * bl.Ltot + bl.plane[l];
     for (int idx = threadIdx.x; idx < CB * Ny; idx += blockDim.x) {
       const int b = idx / Ny, i = idx - b * Ny;
       const int sx = signed_index(kb * CB + b, Nx), sy = signed_index(i, Ny);
@@ -223,6 +226,39 @@ __global__ void k_loss_pointwise(const __grid_constant__ BlasmDev bl, long long 
     const float wd = loss_weight(bl, (int)(lc / bl.C), (int)(r / bl.W), (int)(r % bl.W), t) * d;
     acc = fmaf(wd, d, acc);
     if (dUd) dUd[i] = cscale(u, gscale * wd);
+  }
+  const float tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// Loss and gradient seed of the planes whose propagation is the identity (distance 0, no
+// aperture, every bin inside the band: H = 1 in Algorithm 3, so U(d_l) = U(0)), taken on
+// U(0) itself: per channel c and pixel p, for each such plane l, d = |U|^2 - T_l, the loss
+// partial gains w_l d^2 and the seed sum_l gscale w_l d U (the same seed the loss row pass
+// forms, Sec. 3.2) replaces U when want_grad (each element read and written by one thread).
+__global__ void k_ident_loss(const __grid_constant__ BlasmDev bl, unsigned mask, float gscale,
+                             float2* __restrict__ U, const float* __restrict__ target,
+                             float* __restrict__ partials, int want_grad) {
+  __shared__ float red[32];
+  const long long HW = (long long)bl.H * bl.W, total = HW * bl.C;
+  float acc = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / HW);
+    const long long r = i - (long long)c * HW;
+    const int y = (int)(r / bl.W), x = (int)(r - (long long)y * bl.W);
+    const float2 u = U[i];
+    const float I = fmaf(u.x, u.x, u.y * u.y);
+    float gs = 0.f;
+    for (int l = 0; l < bl.Ltot; ++l) {
+      if (!((mask >> l) & 1u)) continue;
+      const float t = __ldg(&target[((long long)l * bl.C + c) * HW + r]);
+      const float d = I - t;
+      const float wd = loss_weight(bl, l, y, x, t) * d;
+      acc = fmaf(wd, d, acc);
+      gs += wd;
+    }
+    if (want_grad) U[i] = cscale(u, gscale * gs);
   }
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
@@ -330,8 +366,14 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-int rows_loss_blocks(const cgh_plan* p) {
-  return ((p->H + p->row_block - 1) / p->row_block) * p->L * p->C;
+int rows_loss_blocks(const cgh_plan* p, const BlasmDev* planes) {
+  const int L = planes ? planes->L : p->L;
+  return ((p->H + p->row_block - 1) / p->row_block) * L * p->C;
+}
+
+int ident_loss_blocks(const cgh_plan* p) {
+  (void)p;
+  return 592;  // 4 blocks of 256 threads per SM on a 148-152 SM part
 }
 
 int pointwise_loss_blocks(const cgh_plan* p) {
@@ -350,15 +392,15 @@ bool spec_rows(int kind, int N, int RB, int CB, const cgh_plan* p, const SpecRow
          spec_rows_g(kind, N, RB, CB, p, a, s, err, dry);
 }
 
-bool spec_cols(int kind, int N, int CB, const cgh_plan* p, const float2* in, float2* out,
-               cudaStream_t s, cudaError_t* err, bool dry) {
-  return spec_cols_a(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_b(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_c(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_d(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_e(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_f(kind, N, CB, p, in, out, s, err, dry) ||
-         spec_cols_g(kind, N, CB, p, in, out, s, err, dry);
+bool spec_cols(int kind, int N, int CB, const cgh_plan* p, const BlasmDev* bl, const float2* in,
+               float2* out, cudaStream_t s, cudaError_t* err, bool dry) {
+  return spec_cols_a(kind, N, CB, p, bl, in, out, s, err, dry) ||
+         spec_cols_b(kind, N, CB, p, bl, in, out, s, err, dry) ||
+         spec_cols_c(kind, N, CB, p, bl, in, out, s, err, dry) ||
+         spec_cols_d(kind, N, CB, p, bl, in, out, s, err, dry) ||
+         spec_cols_e(kind, N, CB, p, bl, in, out, s, err, dry) ||
+         spec_cols_f(kind, N, CB, p, bl, in, out, s, err, dry) ||
+         spec_cols_g(kind, N, CB, p, bl, in, out, s, err, dry);
 }
 
 static bool try_spec_rows(int kind, cgh_plan* p, const SpecRowArgs& a, cudaStream_t s,
@@ -367,18 +409,18 @@ static bool try_spec_rows(int kind, cgh_plan* p, const SpecRowArgs& a, cudaStrea
   return spec_rows(kind, p->fx.n, p->row_block, p->col_block, p, &a, s, err, false);
 }
 
-static bool try_spec_cols(int kind, cgh_plan* p, const float2* in, float2* out, cudaStream_t s,
-                          cudaError_t* err) {
+static bool try_spec_cols(int kind, cgh_plan* p, const BlasmDev* bl, const float2* in,
+                          float2* out, cudaStream_t s, cudaError_t* err) {
   // the specialised column kernels evaluate H with the series form only
   if (!p->use_spec || !p->bl.series_ok) return false;
-  return spec_cols(kind, p->fy.n, p->col_block, p, in, out, s, err, false);
+  return spec_cols(kind, p->fy.n, p->col_block, p, bl, in, out, s, err, false);
 }
 
 cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,
                                 cudaStream_t s) {
   {
     cudaError_t e;
-    SpecRowArgs a{in, half, nullptr, nullptr, batches, 0, nullptr, nullptr, 0.0};
+    SpecRowArgs a{&p->bl, in, half, nullptr, nullptr, batches, 0, nullptr, nullptr, 0.0, 0, 0};
     if (try_spec_rows(SPEC_ROWS_PAD_FWD, p, a, s, &e)) return e;
   }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
@@ -391,26 +433,30 @@ cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s) {
+cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s,
+                                   const BlasmDev* planes) {
+  const BlasmDev& bl = planes ? *planes : p->bl;
+  if (bl.L == 0) return cudaSuccess;
   {
     cudaError_t e;
-    if (try_spec_cols(SPEC_COLS_FWD_PLANES, p, Y, V, s, &e)) return e;
+    if (try_spec_cols(SPEC_COLS_FWD_PLANES, p, &bl, Y, V, s, &e)) return e;
   }
   const int CB = p->col_block, bs = smem_stride(p->fy.n);
   LaunchShape sh = fft_shape(p, p->fy, CB, 2);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
   dim3 grid(p->bl.Nx / CB, p->C);
   const size_t smem = sizeof(float2) * (size_t)bs * CB * 2;
-  CGH_DISPATCH_MAXB(KID_COLS_FWD_PLANES, sh.maxb, k_cols_fwd_planes, grid, sh.threads, smem, s, p->bl, p->fy, CB, bs,
+  CGH_DISPATCH_MAXB(KID_COLS_FWD_PLANES, sh.maxb, k_cols_fwd_planes, grid, sh.threads, smem, s, bl, p->fy, CB, bs,
                     Y, V);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, int batches,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool accumulate) {
   {
     cudaError_t e;
-    SpecRowArgs a{half, out, nullptr, nullptr, batches, 0};
+    SpecRowArgs a{&p->bl, half, out, nullptr, nullptr, batches, 0, nullptr, nullptr, 0.0, 0,
+                  accumulate ? 1 : 0};
     if (try_spec_rows(SPEC_ROWS_INV_CROP, p, a, s, &e)) return e;
   }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
@@ -419,42 +465,58 @@ cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, i
   dim3 grid((p->H + RB - 1) / RB, batches);
   const size_t smem = sizeof(float2) * (size_t)bs * RB;
   CGH_DISPATCH_MAXB(KID_ROWS_INV_CROP, sh.maxb, k_rows_inv_crop, grid, sh.threads, smem, s, p->bl, p->fx, RB, CB,
-                    bs, half, out);
+                    bs, half, out, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
-                             cudaStream_t s, bool want_grad, float* loss_out) {
+                             cudaStream_t s, bool want_grad, float* loss_out,
+                             const BlasmDev* planes, int extra) {
+  const BlasmDev& bl = planes ? *planes : p->bl;
   const double inv = 1.0 / ((double)p->L * p->C * p->H * p->W);
+  if (bl.L == 0) return launch_loss_finalize(p, partials, extra, loss_out, s);
   {
     cudaError_t e;
-    SpecRowArgs a{nullptr, V, target, partials, p->L * p->C, want_grad ? 1 : 0, loss_out,
-                  (int*)(p->ws + p->off_status) + ST_LOSS_TICKET, inv};
+    SpecRowArgs a{&bl, nullptr, V, target, partials, bl.L * p->C, want_grad ? 1 : 0, loss_out,
+                  (int*)(p->ws + p->off_status) + ST_LOSS_TICKET, inv, extra, 0};
     if (try_spec_rows(SPEC_ROWS_LOSS, p, a, s, &e)) return e;
   }
   const int RB = p->row_block, CB = p->col_block, bs = smem_stride(p->fx.n);
   LaunchShape sh = fft_shape(p, p->fx, RB, 1);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
-  dim3 grid((p->H + RB - 1) / RB, p->L * p->C);
+  dim3 grid((p->H + RB - 1) / RB, bl.L * p->C);
   const size_t smem = sizeof(float2) * (size_t)bs * RB;
-  CGH_DISPATCH_MAXB(KID_ROWS_LOSS, sh.maxb, k_rows_loss, grid, sh.threads, smem, s, p->bl, p->fx, RB, CB, bs,
+  CGH_DISPATCH_MAXB(KID_ROWS_LOSS, sh.maxb, k_rows_loss, grid, sh.threads, smem, s, bl, p->fx, RB, CB, bs,
                     V, target, partials, want_grad ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_loss_finalize(p, partials, rows_loss_blocks(p), loss_out, s);
+  return launch_loss_finalize(p, partials, rows_loss_blocks(p, &bl) + extra, loss_out, s);
 }
 
-cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s) {
+cudaError_t launch_ident_loss(cgh_plan* p, float2* U, const float* target, float* partials,
+                              bool want_grad, cudaStream_t s) {
+  const float gscale = 4.0f / ((float)p->L * (float)p->C * (float)p->H * (float)p->W);
+  prof_begin(KID_IDENT_LOSS, s);
+  k_ident_loss<<<ident_loss_blocks(p), 256, 0, s>>>(p->bl, p->ident_mask, gscale, U, target,
+                                                    partials, want_grad ? 1 : 0);
+  prof_end(KID_IDENT_LOSS, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s,
+                                   const BlasmDev* planes) {
+  const BlasmDev& bl = planes ? *planes : p->bl;
+  if (bl.L == 0) return cudaSuccess;
   {
     cudaError_t e;
-    if (try_spec_cols(SPEC_COLS_BWD_PLANES, p, G, D, s, &e)) return e;
+    if (try_spec_cols(SPEC_COLS_BWD_PLANES, p, &bl, G, D, s, &e)) return e;
   }
   const int CB = p->col_block, bs = smem_stride(p->fy.n);
   LaunchShape sh = fft_shape(p, p->fy, CB, 2);
   if (!sh.ok) return cudaErrorInvalidConfiguration;
   dim3 grid(p->bl.Nx / CB, p->C);
   const size_t smem = sizeof(float2) * (size_t)bs * CB * 2;
-  CGH_DISPATCH_MAXB(KID_COLS_BWD_PLANES, sh.maxb, k_cols_bwd_planes, grid, sh.threads, smem, s, p->bl, p->fy, CB, bs,
+  CGH_DISPATCH_MAXB(KID_COLS_BWD_PLANES, sh.maxb, k_cols_bwd_planes, grid, sh.threads, smem, s, bl, p->fy, CB, bs,
                     G, D);
   return cudaGetLastError();
 }

@@ -153,17 +153,18 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
   return t;  // valid in thread 0
 }
 
-// Loss finalisation by the last CTA of a pass: each CTA has written its partial (thread 0)
-// before calling; the CTA that draws the last ticket sums all `count` partials in FP64 in
-// index order (the result does not depend on which CTA is last), writes sum * inv_norm to
-// out[0] and resets the ticket for the next launch.
-__device__ __forceinline__ void finalize_if_last(const float* partials, int count,
+// Loss finalisation by the last CTA of a pass of `ncta` CTAs: each CTA has written its
+// partial (thread 0) before calling; the CTA that draws the last ticket sums all `count`
+// partials (the pass's own and any written by earlier kernels after them) in FP64 in index
+// order (the result does not depend on which CTA is last), writes sum * inv_norm to out[0]
+// and resets the ticket for the next launch.
+__device__ __forceinline__ void finalize_if_last(const float* partials, int ncta, int count,
                                                  double inv_norm, float* out, int* ticket) {
   __shared__ int s_last;
   __shared__ double s_red[32];
   if (threadIdx.x == 0) {
     __threadfence();  // this CTA's partial is visible before its ticket is
-    s_last = atomicAdd(ticket, 1) == count - 1;
+    s_last = atomicAdd(ticket, 1) == ncta - 1;
   }
   __syncthreads();
   if (!s_last) return;

@@ -85,7 +85,7 @@ template <int N, int R0, int R1, int R2, int NB, int CB, int T>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
                                                       const float2* __restrict__ tw,
                                                       const float2* __restrict__ half,
-                                                      float2* __restrict__ out) {
+                                                      float2* __restrict__ out, int accum) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using I = typename P::I;
   constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), 0);
@@ -104,7 +104,10 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
   float2* dst = out + (size_t)batch * H * W;
   reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
     const int x = a - ox, y = y0 + b;
-    if (x >= 0 && x < W && y < H) dst[(size_t)y * W + x] = val;
+    if (x >= 0 && x < W && y < H) {
+      float2* o = &dst[(size_t)y * W + x];
+      *o = accum ? cadd(*o, val) : val;  // each element is read and written by one thread
+    }
   });
 }
 
@@ -135,7 +138,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
                                                   const float* __restrict__ target,
                                                   float* __restrict__ partials, int want_grad,
                                                   int tstage, float* __restrict__ loss_out,
-                                                  int* __restrict__ ticket, double inv_norm) {
+                                                  int* __restrict__ ticket, double inv_norm,
+                                                  int extra) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using F = typename P::F;
   using I = typename P::I;
@@ -144,10 +148,11 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
   extern __shared__ float2 buf[];
   __shared__ float red[32];
-  const int batch = blockIdx.y, y0 = blockIdx.x * NB;  // batch = l * C + c
+  const int batch = blockIdx.y, y0 = blockIdx.x * NB;  // batch = l * C + c (kernel planes)
   const int H = bl.H, W = bl.W, ox = bl.ox;
+  const int plane = bl.plane[batch / bl.C];  // the hologram plane: target, mask
   float2* half = V + (size_t)batch * H * N;
-  const float* tg = target + (size_t)batch * H * W;
+  const float* tg = target + ((size_t)plane * bl.C + batch % bl.C) * H * W;
   float2* by = buf + P::BUF;  // second exchange buffer (DB)
   float* tsm = reinterpret_cast<float*>(buf + P::BUF + (DB ? P::BUF2 : 0));
   if (tstage) {
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     cp_async_wait_all();
     __syncthreads();
   }
-  const float gscale = 4.0f / ((float)bl.L * (float)bl.C * (float)H * (float)W);
+  const float gscale = 4.0f / ((float)bl.Ltot * (float)bl.C * (float)H * (float)W);
   float acc = 0.f;
   reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
     const int x = a - ox, y = y0 + b;
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
       const float I_ = fmaf(val.x, val.x, val.y * val.y);
       const float t_ = tstage ? tsm[b * W + x] : __ldg(&tg[(size_t)y * W + x]);
       const float d = I_ - t_;
-      const float wd = loss_weight(bl, batch / bl.C, y, x, t_) * d;
+      const float wd = loss_weight(bl, plane, y, x, t_) * d;
       acc = fmaf(wd, d, acc);
       val = cscale(val, gscale * wd);
     } else {
@@ -199,7 +204,9 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     });
   }
   // at the end, where no transform state is live
-  if (loss_out) finalize_if_last(partials, gridDim.x * gridDim.y, inv_norm, loss_out, ticket);
+  if (loss_out)
+    finalize_if_last(partials, gridDim.x * gridDim.y, gridDim.x * gridDim.y + extra, inv_norm,
+                     loss_out, ticket);
 }
 
 // Column kernels work on float4 elements: columns 2 s and 2 s + 1 of the CTA's column block
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
         spec[(i * F::C + r) * T + threadIdx.x] = cscale(S[i][r], bl.inv_ntot);
   }
   for (int l = 0; l < bl.L; ++l) {
-    const TFConst& tc = bl.tf[c * bl.L + l];
+    const TFConst& tc = bl.tf[c * bl.Ltot + bl.plane[l]];
     float4 Z[I::GA::MB][I::A];
 #pragma unroll
     for (int i = 0; i < I::GA::MB; ++i) {
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
   // the running sum over planes lives in thread-private shared-memory slots
   float4* accs = buf4 + P::BUF + (DB ? P::BUF2 : 0);
   for (int l = 0; l < bl.L; ++l) {
-    const TFConst& tc = bl.tf[c * bl.L + l];
+    const TFConst& tc = bl.tf[c * bl.Ltot + bl.plane[l]];
     const float4* src =
         reinterpret_cast<const float4*>(G + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB);
     if (l + 1 < bl.L) {
@@ -382,6 +389,7 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       P::SMEM + (P::db_rows_fits(CGH_REG_MINB(T), 0) ? sizeof(float2) * (size_t)P::BUF2 : 0);
   dim3 grid((p->H + NB - 1) / NB, a->batches);
   const float2* tw = p->fx.tw;
+  const BlasmDev& bl = a->bl ? *a->bl : p->bl;
   cudaError_t e = cudaSuccess;
   switch (kind) {
     case SPEC_ROWS_PAD_FWD: {
@@ -389,7 +397,7 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       e = reg_set_smem(k, smem_db, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_PAD_FWD, s);
-      k<<<grid, T, smem_db, s>>>(p->bl, tw, a->in, a->out);
+      k<<<grid, T, smem_db, s>>>(bl, tw, a->in, a->out);
       prof_end(KID_ROWS_PAD_FWD, s);
       break;
     }
@@ -398,7 +406,7 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       e = reg_set_smem(k, smem_db, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_INV_CROP, s);
-      k<<<grid, T, smem_db, s>>>(p->bl, tw, a->in, a->out);
+      k<<<grid, T, smem_db, s>>>(bl, tw, a->in, a->out, a->accumulate);
       prof_end(KID_ROWS_INV_CROP, s);
       break;
     }
@@ -411,8 +419,8 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_LOSS, s);
-      k<<<grid, T, smem, s>>>(p->bl, tw, a->out, a->target, a->partials, a->want_grad, tstage,
-                              a->loss_out, a->ticket, a->inv_norm);
+      k<<<grid, T, smem, s>>>(bl, tw, a->out, a->target, a->partials, a->want_grad, tstage,
+                              a->loss_out, a->ticket, a->inv_norm, a->extra);
       prof_end(KID_ROWS_LOSS, s);
       break;
     }
@@ -421,24 +429,28 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
 }
 
 template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
-cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float2* out,
-                            cudaStream_t s) {
+cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, const float2* in,
+                            float2* out, cudaStream_t s) {
   using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
   static_assert(P::F::C == P::I::A, "slot layout shared by the forward end and inverse start");
   constexpr size_t smem = P::db_fits(MINB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
-  dim3 grid(p->bl.Nx / (2 * NB), p->C);
+  const BlasmDev& bl = blp ? *blp : p->bl;
+  dim3 grid(bl.Nx / (2 * NB), p->C);
   const float2* tw = p->fy.tw;
   cudaError_t e = cudaSuccess;
-  bool all_in = p->bl.aperture2 <= 0.f;
-  for (int i = 0; i < p->C * p->L; ++i)
-    all_in = all_in && p->bl.tf[i].kx_max >= p->bl.Nx / 2 && p->bl.tf[i].ky_max >= N / 2;
+  bool all_in = bl.aperture2 <= 0.f;
+  for (int c = 0; c < bl.C; ++c)
+    for (int l = 0; l < bl.L; ++l) {
+      const TFConst& t = bl.tf[c * bl.Ltot + bl.plane[l]];
+      all_in = all_in && t.kx_max >= bl.Nx / 2 && t.ky_max >= N / 2;
+    }
   if (kind == SPEC_COLS_FWD_PLANES) {
     auto k = all_in ? kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, true>
                     : kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
     e = reg_set_smem(k, smem, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
-    k<<<grid, T, smem, s>>>(p->bl, tw, in, out);
+    k<<<grid, T, smem, s>>>(bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
     auto k = all_in ? kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, true>
@@ -446,7 +458,7 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
     e = reg_set_smem(k, smem, MINB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
-    k<<<grid, T, smem, s>>>(p->bl, tw, in, out);
+    k<<<grid, T, smem, s>>>(bl, tw, in, out);
     prof_end(KID_COLS_BWD_PLANES, s);
   }
   return cudaGetLastError();
@@ -465,6 +477,6 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const float2* in, float
 //   SM the registers are sized for.
 #define CGH_COL_SPEC(N, R0, R1, R2, NB, T, MINB)                                            \
   if (N_ == N && CB_ == 2 * (NB)) {                                                         \
-    if (!dry) *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T, MINB>(kind, p, in, out, s); \
+    if (!dry) *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T, MINB>(kind, p, bl, in, out, s); \
     return true;                                                                            \
   }

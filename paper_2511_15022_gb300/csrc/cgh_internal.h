@@ -47,8 +47,14 @@ struct TFConst {
   int _pad;
 };
 
+// Geometry, optics and plane map of the propagation kernels.  The row and column passes loop
+// over L planes; plane l of those is plane `plane[l]` of the hologram's Ltot planes, which
+// selects its transfer function (tf[c * Ltot + plane[l]]), its target and depth mask.  The
+// full map (L = Ltot, plane[l] = l) propagates every plane; the map of the fused step leaves
+// out the planes whose propagation is the identity (see cgh_plan::n_ident).
 struct BlasmDev {
   int H, W, C, L;
+  int Ltot;        // planes of the hologram (loss normalisation 1 / (Ltot C H W))
   int Ny, Nx;      // padded sizes
   int oy, ox;      // offset of the image window inside the padded grid
   float inv_ntot;  // 1 / (Ny * Nx)
@@ -56,7 +62,8 @@ struct BlasmDev {
   int series_ok;   // every bin has q = lambda^2 (fx^2 + fy^2) < 0.04 (see transfer_series)
   int loss_kind;   // 0: intensity MSE; 1: three-term L_recon (Sec. 3.2)
   const unsigned char* recon_mask;  // L_recon depth masks [L][H][W] (NULL: M = 0)
-  TFConst tf[CGH_MAX_C * CGH_MAX_L];  // index c * L + l
+  int plane[CGH_MAX_L];                // kernel plane index -> hologram plane
+  TFConst tf[CGH_MAX_C * CGH_MAX_L];  // index c * Ltot + hologram plane
 };
 
 // Per-pixel weight of the loss: (I - T)^2 w.  The three-term L_recon of Sec. 3.2 is
@@ -81,7 +88,15 @@ struct cgh_plan {
   int use_spec;  // 1: use compile-time specialised FFT kernels when one matches
   // FFT descriptors (host copies; tw points into tables_dev)
   FFTDesc fx, fy;
-  BlasmDev bl;
+  BlasmDev bl;       // every plane propagated
+  // Planes at distance 0 with no aperture and every bin inside the band: their transfer
+  // function is exactly 1 (Algorithm 3 with d = 0: phase k_z d = 0, f_max = 1/lambda above
+  // the Nyquist frequency), so U(d_l) = U(0).  The fused step takes their loss and gradient
+  // seed on U(0) in the pixel domain and propagates only the others (bl_prop).
+  int n_ident;
+  unsigned ident_mask;  // bit l: hologram plane l is such a plane
+  int use_ident;        // 1: skip their transforms in the fused step (default); 0: propagate all
+  BlasmDev bl_prop;     // plane map of the planes that are propagated
   // device tables owned by the plan (twiddles)
   void* tables_dev;
   size_t tables_bytes;
@@ -125,17 +140,29 @@ cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* 
                               const cgh_grads* g, cudaStream_t s, bool rebin,
                               const float* grad_scale = nullptr);
 // blasm.cu
+// The column passes and the loss pass take a plane map (NULL: every plane, &p->bl).
 cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,
                                 cudaStream_t s);
-cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s);
+cudaError_t launch_cols_fwd_planes(cgh_plan* p, const float2* Y, float2* V, cudaStream_t s,
+                                   const BlasmDev* planes = nullptr);
+// accumulate: out += the cropped rows (instead of out = ...)
 cudaError_t launch_rows_inv_crop(cgh_plan* p, const float2* half, float2* out, int batches,
-                                 cudaStream_t s);
-// ... and the loss itself: loss_out[0] = sum(partials) / (L C H W), summed in FP64 in a
+                                 cudaStream_t s, bool accumulate = false);
+// ... and the loss itself: loss_out[0] = sum(partials) / (Ltot C H W), summed in FP64 in a
 // fixed order (by the pass's last CTA when a specialised kernel runs, else by
-// k_loss_finalize).
+// k_loss_finalize); `extra` more partials, written before the launch right after the pass's
+// own, are included in the sum.
 cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float* partials,
-                             cudaStream_t s, bool want_grad, float* loss_out);
-cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s);
+                             cudaStream_t s, bool want_grad, float* loss_out,
+                             const BlasmDev* planes = nullptr, int extra = 0);
+cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s,
+                                   const BlasmDev* planes = nullptr);
+// Loss and gradient seed of the identity planes (ident_mask) on U(0), pixel domain: the loss
+// partials go to partials[0, ident_loss_blocks()); with want_grad the seed
+// sum_l 4 w_l (|U|^2 - T_l) U / (Ltot C H W) overwrites U.
+cudaError_t launch_ident_loss(cgh_plan* p, float2* U, const float* target, float* partials,
+                              bool want_grad, cudaStream_t s);
+int ident_loss_blocks(const cgh_plan* p);
 cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* target,
                                   float* partials, float2* dUd, cudaStream_t s);
 cudaError_t launch_loss_finalize(cgh_plan* p, const float* partials, int count, float* out,
@@ -147,7 +174,8 @@ cudaError_t launch_loss_finalize_scaled(const float* partials, int count, double
 cudaError_t launch_intensity(long long total, const float2* U, float* I, cudaStream_t s);
 cudaError_t launch_intensity_bwd(long long total, const float2* U, const float* dI, float2* dU,
                                  cudaStream_t s);
-int rows_loss_blocks(const cgh_plan* p);
+// CTAs of the loss pass over the planes of `planes` (NULL: every plane)
+int rows_loss_blocks(const cgh_plan* p, const BlasmDev* planes = nullptr);
 int pointwise_loss_blocks(const cgh_plan* p);
 // api.cu
 cudaError_t launch_adam(const cgh_adam_group* groups, int n, int step, float b1, float b2,
@@ -163,7 +191,7 @@ enum KernelId {
   KID_PREPROCESS = 0, KID_SCAN_TILES, KID_EMIT, KID_RASTER_FWD, KID_RASTER_BWD,
   KID_GRAD_FINALIZE, KID_ROWS_PAD_FWD, KID_COLS_FWD_PLANES, KID_ROWS_LOSS,
   KID_COLS_BWD_PLANES, KID_ROWS_INV_CROP, KID_LOSS_POINTWISE, KID_LOSS_FINALIZE, KID_ADAM,
-  KID_ENCODER, KID_POH, KID_COUNT
+  KID_ENCODER, KID_POH, KID_IDENT_LOSS, KID_COUNT
 };
 // Bracket one kernel launch: records a CUDA event before and after it on its stream when
 // profiling is enabled; otherwise only the launch counter moves.

@@ -43,3 +43,23 @@ def test_work_model_matches_the_fused_pass_count():
     units_auto = sum(v[0] for k, v in auto.items() if k in field) / (w.C * S) + 3
     assert abs(units_auto - (12 + 8.5 * w.L + 1 + 3 + 2 + 2 * w.L + 2.5 * w.L)) < 1e-9
     assert auto["k_cols_fwd_planes"][3] == 2 and fused["k_cols_fwd_planes"][3] == 1
+
+
+def test_work_model_with_an_identity_plane():
+    """With the plane at 0 mm taken in the pixel domain the column and loss-row passes count
+    the two propagated planes only, and the identity plane's loss pass reads U(0) and one
+    target plane and writes the seed, which the last row pass reads back."""
+    import bench
+    from paper_2511_15022_gb300 import inputs
+    w = inputs.hd_1080p()
+    S = w.H * w.W * 8
+    full = bench.step_work(w, "fused", pairs=0.0)
+    ident = bench.step_work(w, "fused", pairs=0.0, ident=1)
+    assert ident["k_cols_fwd_planes"][0] == (2 + 2 * 2) * w.C * S
+    assert ident["k_cols_bwd_planes"][0] == (2 * 2 + 2) * w.C * S
+    assert ident["k_rows_loss"][0] == 4.5 * 2 * w.C * S
+    assert ident["k_ident_loss"][0] == 2.5 * w.C * S
+    assert ident["k_rows_inv_crop"][0] == full["k_rows_inv_crop"][0] + w.C * S
+    # one column transform of the four per column block fewer in each column pass
+    assert abs(ident["k_cols_fwd_planes"][1] / full["k_cols_fwd_planes"][1] - 3 / 4) < 0.01
+    assert bench.algorithmic_bytes(w, 1)["k_cols_fwd_planes"] == ident["k_cols_fwd_planes"][0]
