@@ -27,7 +27,7 @@ CASES = {
                   0.0, False),
     "two-zero-planes": (inputs.custom(72, 100, 700, wavelengths_m=RGB, z_m=(0.0, 7e-3, 0.0),
                                       seed=44), 0.0, False),
-    "zero-recon-masks": (inputs.custom(90, 110, 900, wavelengths_m=(638e-9, 450e-9),
+    "zero-recon-masks": (inputs.custom(90, 120, 900, wavelengths_m=(638e-9, 450e-9),
                                        z_m=(0.0, 4e-3, 8e-3), seed=45), 0.0, True),
     "zero-with-aperture": (inputs.custom(64, 64, 400, wavelengths_m=(520e-9,),
                                          z_m=(0.0, 5e-3), seed=46), 40.0, False),
