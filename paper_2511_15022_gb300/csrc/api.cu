@@ -93,7 +93,9 @@ static void layout(cgh_plan* p) {
   if (p->pair_capacity > 0x7fffffffLL) p->pair_capacity = 0x7fffffffLL;
   const size_t HW = (size_t)p->H * p->W;
   const size_t half = (size_t)p->H * p->bl.Nx;
-  p->loss_slots = p->H * p->L * p->C + 1024;
+  // loss partials: one per CTA of the loss row pass (at most H L C), plus one per row and
+  // channel of the identity planes' pass
+  p->loss_slots = p->H * p->L * p->C + p->H * p->C + 1024;
   size_t o = 0;
   p->off_rec = o;        o = align256(o + N * CGH_REC_F4 * sizeof(float4));
   p->off_rect = o;       o = align256(o + N * sizeof(int4));

@@ -233,35 +233,36 @@ __global__ void k_loss_pointwise(const __grid_constant__ BlasmDev bl, long long 
 
 // Loss and gradient seed of the planes whose propagation is the identity (distance 0, no
 // aperture, every bin inside the band: H = 1 in Algorithm 3, so U(d_l) = U(0)), taken on
-// U(0) itself: per channel c and pixel p, for each such plane l, d = |U|^2 - T_l, the loss
-// partial gains w_l d^2 and the seed sum_l gscale w_l d U (the same seed the loss row pass
-// forms, Sec. 3.2) replaces U when want_grad (each element read and written by one thread).
-__global__ void k_ident_loss(const __grid_constant__ BlasmDev bl, unsigned mask, float gscale,
-                             float2* __restrict__ U, const float* __restrict__ target,
-                             float* __restrict__ partials, int want_grad) {
+// U(0) itself.  One CTA per image row y (blockIdx.x) and channel c (blockIdx.y); per pixel,
+// for each such plane l, d = |U|^2 - T_l: the loss partial gains w_l d^2 and the seed
+// sum_l gscale w_l d U (the seed the loss row pass forms, Sec. 3.2) replaces U when
+// want_grad (each element read and written by one thread).
+__global__ void __launch_bounds__(256) k_ident_loss(const __grid_constant__ BlasmDev bl,
+                                                    unsigned mask, float gscale,
+                                                    float2* __restrict__ U,
+                                                    const float* __restrict__ target,
+                                                    float* __restrict__ partials, int want_grad) {
   __shared__ float red[32];
-  const long long HW = (long long)bl.H * bl.W, total = HW * bl.C;
+  const int y = blockIdx.x, c = blockIdx.y, W = bl.W;
+  const size_t HW = (size_t)bl.H * W, row = (size_t)c * HW + (size_t)y * W;
+  float2* u_row = U + row;
   float acc = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i / HW);
-    const long long r = i - (long long)c * HW;
-    const int y = (int)(r / bl.W), x = (int)(r - (long long)y * bl.W);
-    const float2 u = U[i];
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    const float2 u = u_row[x];
     const float I = fmaf(u.x, u.x, u.y * u.y);
     float gs = 0.f;
     for (int l = 0; l < bl.Ltot; ++l) {
       if (!((mask >> l) & 1u)) continue;
-      const float t = __ldg(&target[((long long)l * bl.C + c) * HW + r]);
+      const float t = __ldg(&target[(size_t)l * bl.C * HW + row + x]);
       const float d = I - t;
       const float wd = loss_weight(bl, l, y, x, t) * d;
       acc = fmaf(wd, d, acc);
       gs += wd;
     }
-    if (want_grad) U[i] = cscale(u, gscale * gs);
+    if (want_grad) u_row[x] = cscale(u, gscale * gs);
   }
   const float tot = block_sum(acc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
 // Intensity of a complex field (Sec. 3.2: I = |U|^2), element-wise over `total` values.
@@ -371,10 +372,7 @@ int rows_loss_blocks(const cgh_plan* p, const BlasmDev* planes) {
   return ((p->H + p->row_block - 1) / p->row_block) * L * p->C;
 }
 
-int ident_loss_blocks(const cgh_plan* p) {
-  (void)p;
-  return 592;  // 4 blocks of 256 threads per SM on a 148-152 SM part
-}
+int ident_loss_blocks(const cgh_plan* p) { return p->H * p->C; }  // one per row and channel
 
 int pointwise_loss_blocks(const cgh_plan* p) {
   (void)p;
@@ -497,8 +495,8 @@ cudaError_t launch_ident_loss(cgh_plan* p, float2* U, const float* target, float
                               bool want_grad, cudaStream_t s) {
   const float gscale = 4.0f / ((float)p->L * (float)p->C * (float)p->H * (float)p->W);
   prof_begin(KID_IDENT_LOSS, s);
-  k_ident_loss<<<ident_loss_blocks(p), 256, 0, s>>>(p->bl, p->ident_mask, gscale, U, target,
-                                                    partials, want_grad ? 1 : 0);
+  k_ident_loss<<<dim3(p->H, p->C), 256, 0, s>>>(p->bl, p->ident_mask, gscale, U, target,
+                                                partials, want_grad ? 1 : 0);
   prof_end(KID_IDENT_LOSS, s);
   return cudaGetLastError();
 }

@@ -81,36 +81,6 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __gr
   });
 }
 
-template <int N, int R0, int R1, int R2, int NB, int CB, int T>
-__global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
-                                                      const float2* __restrict__ tw,
-                                                      const float2* __restrict__ half,
-                                                      float2* __restrict__ out, int accum) {
-  using P = RegPlan<N, R0, R1, R2, NB, T>;
-  using I = typename P::I;
-  constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), 0);
-  extern __shared__ float2 buf[];
-  const int batch = blockIdx.y, y0 = blockIdx.x * NB;
-  const int H = bl.H, W = bl.W, ox = bl.ox;
-  const float2* src = half + (size_t)batch * H * N;
-  float2 v[I::GA::MB][I::A];
-  reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
-    const int y = y0 + b;
-    return y < H ? __ldg(&src[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
-  });
-  float2 u[I::GC::MB][I::C];
-  if constexpr (DB) I::rest2(v, u, buf, buf + P::BUF, tw);
-  else I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
-  float2* dst = out + (size_t)batch * H * W;
-  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
-    const int x = a - ox, y = y0 + b;
-    if (x >= 0 && x < W && y < H) {
-      float2* o = &dst[(size_t)y * W + x];
-      *o = accum ? cadd(*o, val) : val;  // each element is read and written by one thread
-    }
-  });
-}
-
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
                    static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst))),
@@ -122,6 +92,60 @@ __device__ __forceinline__ void cp_async_commit() {
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// largest addend stage of kr_rows_inv_crop (NB rows of W = N / 2 complex values)
+template <int N, int NB>
+constexpr size_t rows_addend_bytes() { return sizeof(float2) * (size_t)NB * (N / 2); }
+
+// accum = 0: out = the cropped rows.  accum = 1: out += them, the CTA's NB rows of `out`
+// staged in shared memory (after the exchange buffers) by asynchronous 16-byte copies issued
+// before the transform, so their latency hides behind it (needs W even and a 16-byte
+// aligned `out`); accum = 2: out += them with plain loads in the epilogue.
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool ACC>
+__global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
+                                                      const float2* __restrict__ tw,
+                                                      const float2* __restrict__ half,
+                                                      float2* __restrict__ out, int accum) {
+  using P = RegPlan<N, R0, R1, R2, NB, T>;
+  using I = typename P::I;
+  constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), ACC ? rows_addend_bytes<N, NB>() : 0);
+  if (!ACC) accum = 0;
+  extern __shared__ float2 buf[];
+  const int batch = blockIdx.y, y0 = blockIdx.x * NB;
+  const int H = bl.H, W = bl.W, ox = bl.ox;
+  const float2* src = half + (size_t)batch * H * N;
+  float2* dst = out + (size_t)batch * H * W;
+  float2* asm_ = buf + P::BUF + (DB ? P::BUF2 : 0);  // addend stage (accum = 1)
+  if (accum == 1) {
+    const int chunks = NB * (W / 2);
+    for (int i = threadIdx.x; i < chunks; i += T) {
+      const int b = i / (W / 2), x = (i % (W / 2)) * 2;
+      if (y0 + b < H) cp_async16(&asm_[b * W + x], &dst[(size_t)(y0 + b) * W + x]);
+    }
+    cp_async_commit();
+  }
+  float2 v[I::GA::MB][I::A];
+  reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
+    const int y = y0 + b;
+    return y < H ? __ldg(&src[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
+  });
+  float2 u[I::GC::MB][I::C];
+  if constexpr (DB) I::rest2(v, u, buf, buf + P::BUF, tw);
+  else I::template rest<false>(v, u, buf, tw);  // first transform: no earlier reader
+  if (accum == 1) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
+    const int x = a - ox, y = y0 + b;
+    if (x >= 0 && x < W && y < H) {
+      float2* o = &dst[(size_t)y * W + x];
+      if (accum == 1) val = cadd(asm_[b * W + x], val);
+      else if (accum == 2) val = cadd(*o, val);  // each element read and written by one thread
+      *o = val;
+    }
+  });
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -387,6 +411,9 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   constexpr size_t smem_db =
       P::SMEM + (P::db_rows_fits(CGH_REG_MINB(T), 0) ? sizeof(float2) * (size_t)P::BUF2 : 0);
+  // accumulating rows_inv_crop: exchange buffers as that kernel sizes them, plus the stage
+  constexpr bool db_acc = P::db_rows_fits(CGH_REG_MINB(T), rows_addend_bytes<N, NB>());
+  constexpr size_t smem_acc = P::SMEM + (db_acc ? sizeof(float2) * (size_t)P::BUF2 : 0);
   dim3 grid((p->H + NB - 1) / NB, a->batches);
   const float2* tw = p->fx.tw;
   const BlasmDev& bl = a->bl ? *a->bl : p->bl;
@@ -402,11 +429,17 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       break;
     }
     case SPEC_ROWS_INV_CROP: {
-      auto k = kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T>;
-      e = reg_set_smem(k, smem_db, CGH_REG_MINB(T));
+      auto k = a->accumulate ? kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T, true>
+                             : kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T, false>;
+      const bool stage = a->accumulate && p->W % 2 == 0 &&
+                         (reinterpret_cast<uintptr_t>(a->out) & 15u) == 0;
+      const int accum = a->accumulate ? (stage ? 1 : 2) : 0;
+      const size_t smem = a->accumulate ? smem_acc + (stage ? sizeof(float2) * (size_t)NB * p->W : 0)
+                                        : smem_db;
+      e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_INV_CROP, s);
-      k<<<grid, T, smem_db, s>>>(bl, tw, a->in, a->out, a->accumulate);
+      k<<<grid, T, smem, s>>>(bl, tw, a->in, a->out, accum);
       prof_end(KID_ROWS_INV_CROP, s);
       break;
     }
