@@ -330,20 +330,23 @@ cgh_status cgh_autotune(cgh_plan* plan, const cgh_params* params, const float* t
 
 /* ---- learned initialiser (the paper has no learned part; it lists feed-forward prediction
  * as future work, Sec. 6): a stack of 3x3 convolutions with BF16 weights and activations
- * (16-bit bfloat16 values passed as void*) and FP32 accumulation, and the decode from the
- * last layer to Gaussian parameters.
+ * (16-bit bfloat16 values passed as void*) and FP32 accumulation, run on the tensor cores,
+ * and the decode from the last layer to Gaussian parameters.
  *
  * cgh_conv3x3_fwd: y[b][co][oy][ox] = act(bias[co] + sum_{ci,ky,kx} w[co][ci][ky][kx]
  *   x[b][ci][oy*stride+ky-1][ox*stride+kx-1]) (zero outside the image), act = ReLU if relu.
  *   x: [B][CI][Hi][Wi] bf16; w: [CO][CI][3][3] bf16; bias: [CO] f32; y: [B][CO][Ho][Wo] with
- *   Ho = (Hi-1)/stride + 1, bf16 or f32 (y_f32).  CI <= 170. */
+ *   Ho = (Hi-1)/stride + 1, bf16 or f32 (y_f32).  stride 1 or 2 (else
+ *   CGH_ERR_UNSUPPORTED_SIZE).  The products of the BF16 operands are exact in FP32. */
 cgh_status cgh_conv3x3_fwd(int32_t B, int32_t CI, int32_t Hi, int32_t Wi, int32_t CO,
                            int32_t stride, const void* x, const void* w, const float* bias,
                            int32_t relu, void* y, int32_t y_f32, void* stream);
 
 /* Backward of cgh_conv3x3_fwd given dy = dL/dy (f32, same layout as y) and the forward
  * output y (needed for the ReLU mask when relu = 1): dx = dL/dx (f32, may be NULL to skip),
- * dw = dL/dw [CO][CI][3][3] f32 and db = dL/dbias [CO] f32 (both overwritten).  CO <= 340. */
+ * dw = dL/dw [CO][CI][3][3] f32 and db = dL/dbias [CO] f32 (both overwritten).  The FP32
+ * gradient g = dy [y > 0] enters the tensor-core products as two BF16 parts hi = bf16(g),
+ * lo = bf16(g - hi), which represent it to 2^-18 relative; stride 1 or 2. */
 cgh_status cgh_conv3x3_bwd(int32_t B, int32_t CI, int32_t Hi, int32_t Wi, int32_t CO,
                            int32_t stride, const void* x, const void* w, int32_t relu,
                            const void* y, int32_t y_f32, const float* dy, float* dx, float* dw,

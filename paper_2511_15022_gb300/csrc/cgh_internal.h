@@ -177,6 +177,17 @@ cudaError_t launch_intensity_bwd(long long total, const float2* U, const float* 
 // CTAs of the loss pass over the planes of `planes` (NULL: every plane)
 int rows_loss_blocks(const cgh_plan* p, const BlasmDev* planes = nullptr);
 int pointwise_loss_blocks(const cgh_plan* p);
+// conv_tc.cu: tensor-core 3x3 convolutions (strides 1 and 2) of the learned initialiser
+cudaError_t conv3x3_fwd_tc(int B, int CI, int Hi, int Wi, int CO, int stride, const void* x,
+                           const void* w, const float* bias, int relu, void* y, int y_f32,
+                           cudaStream_t s);
+cudaError_t conv3x3_dgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, const void* w,
+                             int relu, const void* y, int y_f32, const float* dy, float* dx,
+                             cudaStream_t s);
+// adds into dw [CO][CI][9] and db [CO] (zero them first)
+cudaError_t conv3x3_wgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, const void* x,
+                             int relu, const void* y, int y_f32, const float* dy, float* dw,
+                             float* db, cudaStream_t s);
 // api.cu
 cudaError_t launch_adam(const cgh_adam_group* groups, int n, int step, float b1, float b2,
                         float eps, cudaStream_t s);

@@ -1,0 +1,396 @@
+// conv_tc.cu -- tensor-core 3x3 convolutions of the learned initialiser (sm_103a).
+//
+// The encoder's convolutions are dense contractions, so they run on the tensor cores as
+// implicit GEMMs: warp-level mma.sync m16n8k16 with BF16 operands and FP32 accumulation,
+// operands staged in shared memory and loaded into fragments with ldmatrix.
+//
+//   k_conv_tc<MODE_FWD>   y = act(bias + W * x): one CTA per 8 x 16 tile of output pixels and
+//                         64 output channels; the input patch of each 16-channel chunk is
+//                         staged channel-innermost ([position][channel]), so the 16 pixels x
+//                         16 channels A fragment of one filter tap is one ldmatrix.x4 of 16
+//                         rows (the im2col gather happens in the row addresses); weights are
+//                         staged [tap][out channel][channel] (the B fragments).
+//   k_conv_tc<MODE_DGRAD> dx = W^T * g with g = dy [y > 0]: for a stride-s convolution this is
+//                         the stride-1 convolution of g zero-upsampled by s with the transposed,
+//                         flipped weights W'[ci][co][2-ky][2-kx]; the same kernel stages that
+//                         virtual input.  g is FP32, so it is split into two BF16 parts, hi =
+//                         bf16(g) and lo = bf16(g - hi) (|g - hi - lo| <= 2^-18 |g|), and both
+//                         are multiplied: the product keeps FP32 accuracy.
+//   k_conv_wgrad_tc       dW[co][ci][tap] = sum over pixels of g x_shifted, db[co] = sum g:
+//                         M = 64 output channels, N = 16 input channels x 9 taps, K = pixels
+//                         (16 per step, one output row of a tile); each CTA walks a range of
+//                         pixel tiles, accumulating in registers, and adds its partial sums
+//                         with one atomic per value.  g is split as above.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cgh_internal.h"
+
+namespace cgh {
+namespace tc {
+
+constexpr int TH = 8, TW = 16;  // output pixel tile: one warp per row of 16 pixels
+constexpr int NT = 64;          // output channels per CTA (8 n8 blocks)
+constexpr int KC = 16;          // channels per staged chunk (one k16 step per tap)
+constexpr int PS = 24;          // bf16 per staged position / weight row: 48-byte rows, 16-byte
+                                // aligned for ldmatrix, consecutive rows on different banks
+constexpr int kThreads = 256;
+constexpr int GS = TH * TW + 8; // bf16 per staged row of the weight-gradient tiles (272 bytes)
+
+enum { MODE_FWD = 0, MODE_DGRAD = 1 };
+
+struct ConvArgs {
+  int B;
+  int Kc, Nc;        // contraction channels (per tap) and output channels of this convolution
+  int Hin, Win;      // the convolution's input grid (DGRAD: the zero-upsampled g, s * Ho x s * Wo)
+  int Hout, Wout;    // output grid
+  int sc;            // convolution stride (FWD: s; DGRAD: 1)
+  int up;            // DGRAD: upsampling factor s of g
+  int Hg, Wg;        // DGRAD: grid of g (Ho x Wo)
+  int relu, y_f32, out_f32;
+  const __nv_bfloat16* x;  // FWD input [B][Kc][Hin][Win]
+  const float* dy;         // DGRAD upstream gradient [B][Kc][Hg][Wg]
+  const void* y;           // DGRAD: forward output of the layer (ReLU mask), same layout as dy
+  const __nv_bfloat16* w;  // forward weights [CO][CI][3][3]
+  const float* bias;       // FWD
+  void* out;               // [B][Nc][Hout][Wout], bf16 or f32
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(addr));
+}
+
+// D = A B + D, A 16 x 16 (row), B 16 x 8 (col), BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// g = dy [y > 0] (no mask without ReLU)
+__device__ __forceinline__ float grad_in(const float* dy, const void* y, int y_f32, int relu,
+                                         size_t o) {
+  float g = __ldg(&dy[o]);
+  if (relu) {
+    const float yv = y_f32 ? __ldg(&static_cast<const float*>(y)[o])
+                           : __bfloat162float(static_cast<const __nv_bfloat16*>(y)[o]);
+    if (!(yv > 0.f)) g = 0.f;
+  }
+  return g;
+}
+
+__device__ __forceinline__ void split_bf16(float g, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(g);
+  lo = __float2bfloat16_rn(g - __bfloat162float(hi));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
+  constexpr int NPART = MODE == MODE_DGRAD ? 2 : 1;  // hi / lo parts of the input
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int sc = a.sc;
+  const int PH = (TH - 1) * sc + 3, PW = (TW - 1) * sc + 3;
+  __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [9][NT][PS]
+  __nv_bfloat16* patch = wt + 9 * NT * PS;                           // [NPART][PH * PW][PS]
+  const int npos = PH * PW;
+  const int ntx = (a.Wout + TW - 1) / TW;
+  const int ox0 = (blockIdx.x % ntx) * TW, oy0 = (blockIdx.x / ntx) * TH;
+  const int nblk = (a.Nc + NT - 1) / NT;
+  const int b = blockIdx.y / nblk, n0 = (blockIdx.y % nblk) * NT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int iy0 = oy0 * sc - 1, ix0 = ox0 * sc - 1;  // input position of patch (0, 0)
+
+  float acc[NT / 8][4];
+#pragma unroll
+  for (int j = 0; j < NT / 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+
+  for (int c0 = 0; c0 < a.Kc; c0 += KC) {
+    __syncthreads();  // the previous chunk's fragments have been loaded
+    // weights of this chunk: wt[tap][n][c] = W(n0 + n, c0 + c, tap)
+    for (int e = threadIdx.x; e < 9 * NT * KC; e += kThreads) {
+      const int c = e % KC, n = (e / KC) % NT, tap = e / (KC * NT);
+      const int nn = n0 + n, cc = c0 + c;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (nn < a.Nc && cc < a.Kc) {
+        if (MODE == MODE_FWD) v = a.w[((size_t)nn * a.Kc + cc) * 9 + tap];
+        else v = a.w[((size_t)cc * a.Nc + nn) * 9 + (8 - tap)];  // transposed, flipped
+      }
+      wt[(tap * NT + n) * PS + c] = v;
+    }
+    // the input patch of this chunk, channel-innermost
+    for (int e = threadIdx.x; e < KC * npos; e += kThreads) {
+      const int pos = e % npos, c = e / npos, cc = c0 + c;
+      const int Y = iy0 + pos / PW, X = ix0 + pos % PW;
+      if (MODE == MODE_FWD) {
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (cc < a.Kc && Y >= 0 && Y < a.Hin && X >= 0 && X < a.Win)
+          v = a.x[(((size_t)b * a.Kc + cc) * a.Hin + Y) * a.Win + X];
+        patch[pos * PS + c] = v;
+      } else {
+        float g = 0.f;
+        if (cc < a.Kc && Y >= 0 && X >= 0 && Y % a.up == 0 && X % a.up == 0) {
+          const int gy = Y / a.up, gx = X / a.up;
+          if (gy < a.Hg && gx < a.Wg)
+            g = grad_in(a.dy, a.y, a.y_f32, a.relu,
+                        (((size_t)b * a.Kc + cc) * a.Hg + gy) * a.Wg + gx);
+        }
+        __nv_bfloat16 hi, lo;
+        split_bf16(g, hi, lo);
+        patch[pos * PS + c] = hi;
+        patch[(npos + pos) * PS + c] = lo;
+      }
+    }
+    __syncthreads();
+    // warp `warp` computes output row oy0 + warp: A rows are its 16 pixels
+    const int arow = lane & 15, akh = lane >> 4;
+    const int bn = (lane & 7) + ((lane >> 4) << 3), bkh = (lane >> 3) & 1;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
+      const int pos = (warp * sc + ky) * PW + arow * sc + kx;
+      uint32_t af[NPART][4];
+#pragma unroll
+      for (int part = 0; part < NPART; ++part)
+        ldsm_x4(af[part], smem_u32(&patch[(part * npos + pos) * PS + akh * 8]));
+#pragma unroll
+      for (int j = 0; j < NT / 16; ++j) {  // two n8 blocks per ldmatrix.x4
+        uint32_t bf[4];
+        ldsm_x4(bf, smem_u32(&wt[(tap * NT + 16 * j + bn) * PS + bkh * 8]));
+#pragma unroll
+        for (int part = 0; part < NPART; ++part) {
+          mma_bf16(acc[2 * j], af[part], bf[0], bf[1]);
+          mma_bf16(acc[2 * j + 1], af[part], bf[2], bf[3]);
+        }
+      }
+    }
+  }
+  // epilogue: acc[j] = (pixel g, channels 8j + 2t, +1) and (pixel g + 8, ...)
+  const int oy = oy0 + warp, gq = lane >> 2, tq = lane & 3;
+  if (oy >= a.Hout) return;
+#pragma unroll
+  for (int j = 0; j < NT / 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = n0 + 8 * j + 2 * tq + (q & 1);
+      const int ox = ox0 + gq + ((q >> 1) << 3);
+      if (n >= a.Nc || ox >= a.Wout) continue;
+      float v = acc[j][q];
+      if (MODE == MODE_FWD) {
+        v += __ldg(&a.bias[n]);
+        if (a.relu) v = fmaxf(v, 0.f);
+      }
+      const size_t o = (((size_t)b * a.Nc + n) * a.Hout + oy) * a.Wout + ox;
+      if (a.out_f32) static_cast<float*>(a.out)[o] = v;
+      else static_cast<__nv_bfloat16*>(a.out)[o] = __float2bfloat16_rn(v);
+    }
+}
+
+struct WgradArgs {
+  int B, CI, Hi, Wi, CO, Ho, Wo, stride, relu, y_f32;
+  int per_cta;  // pixel tiles per CTA
+  const __nv_bfloat16* x;
+  const void* y;
+  const float* dy;
+  float* dw;
+  float* db;
+};
+
+// dW partial sums of one CTA: co block blockIdx.y (64 channels), ci chunk blockIdx.z (16
+// channels x 9 taps), pixel tiles [blockIdx.x * per_cta, +per_cta).  Warp w: m16 block w & 3
+// (16 output channels), n8 blocks 9 (w >> 2) .. + 9 of the 18 (tap, ci) blocks.
+__global__ void __launch_bounds__(kThreads) k_conv_wgrad_tc(WgradArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* gs = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [2][NT][GS] g hi / lo
+  __nv_bfloat16* xs = gs + 2 * NT * GS;                              // [9 * KC][GS] shifted x
+  const int co0 = blockIdx.y * NT, ci0 = blockIdx.z * KC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mb = warp & 3, nb0 = 9 * (warp >> 2);
+  const int ntx = (a.Wo + TW - 1) / TW, nty = (a.Ho + TH - 1) / TH;
+  const long long tiles = (long long)a.B * ntx * nty;
+  const long long t0 = (long long)blockIdx.x * a.per_cta;
+  const long long t1 = t0 + a.per_cta < tiles ? t0 + a.per_cta : tiles;
+  float acc[9][4];
+#pragma unroll
+  for (int j = 0; j < 9; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+  float dbsum = 0.f;  // warp w: channels co0 + 8 w .. + 8 (lane & 7), lanes 0-7 hold them
+  for (long long t = t0; t < t1; ++t) {
+    const int b = (int)(t / ((long long)ntx * nty));
+    const int r = (int)(t % ((long long)ntx * nty));
+    const int oy0 = (r / ntx) * TH, ox0 = (r % ntx) * TW;
+    __syncthreads();  // the previous tile's fragments have been loaded
+    for (int e = threadIdx.x; e < NT * TH * TW; e += kThreads) {
+      const int p = e % (TH * TW), co = e / (TH * TW);
+      const int oy = oy0 + p / TW, ox = ox0 + p % TW;
+      float g = 0.f;
+      if (co0 + co < a.CO && oy < a.Ho && ox < a.Wo)
+        g = grad_in(a.dy, a.y, a.y_f32, a.relu,
+                    (((size_t)b * a.CO + co0 + co) * a.Ho + oy) * a.Wo + ox);
+      __nv_bfloat16 hi, lo;
+      split_bf16(g, hi, lo);
+      gs[co * GS + p] = hi;
+      gs[(NT + co) * GS + p] = lo;
+    }
+    for (int e = threadIdx.x; e < 9 * KC * TH * TW; e += kThreads) {
+      const int p = e % (TH * TW), row = e / (TH * TW);  // row = tap * KC + ci
+      const int tap = row / KC, ci = ci0 + row % KC;
+      const int oy = oy0 + p / TW, ox = ox0 + p % TW;
+      const int iy = oy * a.stride + tap / 3 - 1, ix = ox * a.stride + tap % 3 - 1;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (ci < a.CI && oy < a.Ho && ox < a.Wo && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi)
+        v = a.x[(((size_t)b * a.CI + ci) * a.Hi + iy) * a.Wi + ix];
+      xs[row * GS + p] = v;
+    }
+    __syncthreads();
+    if (blockIdx.z == 0 && lane < 8) {  // bias gradient: FP32 sum of hi + lo
+      const int co = 8 * warp + lane;
+      float s = 0.f;
+      for (int p = 0; p < TH * TW; ++p)
+        s += __bfloat162float(gs[co * GS + p]) + __bfloat162float(gs[(NT + co) * GS + p]);
+      dbsum += s;
+    }
+#pragma unroll
+    for (int ks = 0; ks < TH * TW / 16; ++ks) {
+      uint32_t af[2][4];
+      const int arow = 16 * mb + (lane & 15), ak = 16 * ks + 8 * (lane >> 4);
+#pragma unroll
+      for (int part = 0; part < 2; ++part)
+        ldsm_x4(af[part], smem_u32(&gs[(part * NT + arow) * GS + ak]));
+      const int bk = 16 * ks + 8 * ((lane >> 3) & 1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // n8 blocks nb0 + 2j, + 1
+        uint32_t bf[4];
+        const int n = 8 * (nb0 + 2 * j) + (lane & 7) + ((lane >> 4) << 3);
+        ldsm_x4(bf, smem_u32(&xs[n * GS + bk]));
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          mma_bf16(acc[2 * j], af[part], bf[0], bf[1]);
+          mma_bf16(acc[2 * j + 1], af[part], bf[2], bf[3]);
+        }
+      }
+      {  // the ninth n8 block
+        uint32_t bf[2];
+        const int n = 8 * (nb0 + 8) + (lane & 7);
+        ldsm_x2(bf, smem_u32(&xs[n * GS + bk]));
+#pragma unroll
+        for (int part = 0; part < 2; ++part) mma_bf16(acc[8], af[part], bf[0], bf[1]);
+      }
+    }
+  }
+  // partial sums to global: acc[j] = (co 16 mb + g (+8), n = 8 (nb0 + j) + 2t, +1)
+  const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 9; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int co = co0 + 16 * mb + gq + ((q >> 1) << 3);
+      const int n = 8 * (nb0 + j) + 2 * tq + (q & 1);
+      const int tap = n / KC, ci = ci0 + n % KC;
+      if (co < a.CO && ci < a.CI && acc[j][q] != 0.f)
+        atomicAdd(&a.dw[((size_t)co * a.CI + ci) * 9 + tap], acc[j][q]);
+    }
+  if (blockIdx.z == 0 && lane < 8 && co0 + 8 * warp + lane < a.CO && dbsum != 0.f)
+    atomicAdd(&a.db[co0 + 8 * warp + lane], dbsum);
+}
+
+}  // namespace tc
+}  // namespace cgh
+
+using namespace cgh;
+
+namespace {
+
+size_t conv_smem_bytes(int mode, int sc) {
+  const int PH = (tc::TH - 1) * sc + 3, PW = (tc::TW - 1) * sc + 3;
+  return sizeof(__nv_bfloat16) * ((size_t)9 * tc::NT * tc::PS +
+                                  (size_t)(mode == tc::MODE_DGRAD ? 2 : 1) * PH * PW * tc::PS);
+}
+
+template <int MODE>
+cudaError_t launch_conv_tc(const tc::ConvArgs& a, cudaStream_t s) {
+  const size_t smem = conv_smem_bytes(MODE, a.sc);
+  cudaError_t e = cudaFuncSetAttribute(tc::k_conv_tc<MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int tiles = ((a.Hout + tc::TH - 1) / tc::TH) * ((a.Wout + tc::TW - 1) / tc::TW);
+  dim3 grid(tiles, a.B * ((a.Nc + tc::NT - 1) / tc::NT));
+  prof_begin(KID_ENCODER, s);
+  tc::k_conv_tc<MODE><<<grid, tc::kThreads, smem, s>>>(a);
+  prof_end(KID_ENCODER, s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tensor-core forward convolution (strides 1 and 2); see encoder.cu for the entry point.
+cudaError_t conv3x3_fwd_tc(int B, int CI, int Hi, int Wi, int CO, int stride,
+                           const void* x, const void* w, const float* bias, int relu, void* y,
+                           int y_f32, cudaStream_t s) {
+  tc::ConvArgs a = {};
+  a.B = B; a.Kc = CI; a.Nc = CO; a.Hin = Hi; a.Win = Wi;
+  a.Hout = (Hi - 1) / stride + 1; a.Wout = (Wi - 1) / stride + 1;
+  a.sc = stride; a.up = 1; a.relu = relu; a.out_f32 = y_f32;
+  a.x = (const __nv_bfloat16*)x; a.w = (const __nv_bfloat16*)w; a.bias = bias; a.out = y;
+  return launch_conv_tc<tc::MODE_FWD>(a, s);
+}
+
+// Tensor-core data gradient dx (f32) of a stride-`stride` convolution (strides 1 and 2).
+cudaError_t conv3x3_dgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, const void* w,
+                             int relu, const void* y, int y_f32, const float* dy, float* dx,
+                             cudaStream_t s) {
+  tc::ConvArgs a = {};
+  a.B = B; a.Kc = CO; a.Nc = CI;
+  a.Hg = (Hi - 1) / stride + 1; a.Wg = (Wi - 1) / stride + 1;
+  a.Hin = a.Hg * stride; a.Win = a.Wg * stride;
+  a.Hout = Hi; a.Wout = Wi; a.sc = 1; a.up = stride;
+  a.relu = relu; a.y_f32 = y_f32; a.out_f32 = 1;
+  a.dy = dy; a.y = y; a.w = (const __nv_bfloat16*)w; a.out = dx;
+  return launch_conv_tc<tc::MODE_DGRAD>(a, s);
+}
+
+// Tensor-core weight and bias gradients (accumulated into dw, db with atomics).
+cudaError_t conv3x3_wgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, const void* x,
+                             int relu, const void* y, int y_f32, const float* dy, float* dw,
+                             float* db, cudaStream_t s) {
+  tc::WgradArgs a = {};
+  a.B = B; a.CI = CI; a.Hi = Hi; a.Wi = Wi; a.CO = CO;
+  a.Ho = (Hi - 1) / stride + 1; a.Wo = (Wi - 1) / stride + 1;
+  a.stride = stride; a.relu = relu; a.y_f32 = y_f32;
+  a.x = (const __nv_bfloat16*)x; a.y = y; a.dy = dy; a.dw = dw; a.db = db;
+  const long long tiles = (long long)B * ((a.Ho + tc::TH - 1) / tc::TH) *
+                          ((a.Wo + tc::TW - 1) / tc::TW);
+  const int cob = (CO + tc::NT - 1) / tc::NT, cib = (CI + tc::KC - 1) / tc::KC;
+  // about two CTAs per SM over all (co block, ci chunk) pairs, at least 4 tiles each
+  long long ctas = (2LL * 152 + cob * cib - 1) / (cob * cib);
+  long long per = (tiles + ctas - 1) / ctas;
+  if (per < 4) per = 4;
+  ctas = (tiles + per - 1) / per;
+  a.per_cta = (int)per;
+  const size_t smem = sizeof(__nv_bfloat16) * ((size_t)2 * tc::NT + 9 * tc::KC) * tc::GS;
+  cudaError_t e = cudaFuncSetAttribute(tc::k_conv_wgrad_tc,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  prof_begin(KID_ENCODER, s);
+  tc::k_conv_wgrad_tc<<<dim3((unsigned)ctas, cob, cib), tc::kThreads, smem, s>>>(a);
+  prof_end(KID_ENCODER, s);
+  return cudaGetLastError();
+}
