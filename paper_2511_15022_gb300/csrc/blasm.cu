@@ -236,7 +236,10 @@ __global__ void k_loss_pointwise(const __grid_constant__ BlasmDev bl, long long 
 // U(0) itself.  One CTA per image row y (blockIdx.x) and channel c (blockIdx.y); per pixel,
 // for each such plane l, d = |U|^2 - T_l: the loss partial gains w_l d^2 and the seed
 // sum_l gscale w_l d U (the seed the loss row pass forms, Sec. 3.2) replaces U when
-// want_grad (each element read and written by one thread).
+// want_grad (each element read and written by one thread).  Each thread loads its kIdentU
+// elements of a row before using any (a 1920-pixel row is one round), so enough loads are
+// in flight to cover the memory latency.
+constexpr int kIdentU = 8;
 __global__ void __launch_bounds__(256) k_ident_loss(const __grid_constant__ BlasmDev bl,
                                                     unsigned mask, float gscale,
                                                     float2* __restrict__ U,
@@ -247,19 +250,41 @@ __global__ void __launch_bounds__(256) k_ident_loss(const __grid_constant__ Blas
   const size_t HW = (size_t)bl.H * W, row = (size_t)c * HW + (size_t)y * W;
   float2* u_row = U + row;
   float acc = 0.f;
-  for (int x = threadIdx.x; x < W; x += blockDim.x) {
-    const float2 u = u_row[x];
-    const float I = fmaf(u.x, u.x, u.y * u.y);
-    float gs = 0.f;
+  for (int x0 = 0; x0 < W; x0 += kIdentU * 256) {
+    float2 u[kIdentU];
+    float gs[kIdentU];
+#pragma unroll
+    for (int k = 0; k < kIdentU; ++k) {
+      const int x = x0 + k * 256 + threadIdx.x;
+      u[k] = x < W ? u_row[x] : make_float2(0.f, 0.f);
+      gs[k] = 0.f;
+    }
     for (int l = 0; l < bl.Ltot; ++l) {
       if (!((mask >> l) & 1u)) continue;
-      const float t = __ldg(&target[(size_t)l * bl.C * HW + row + x]);
-      const float d = I - t;
-      const float wd = loss_weight(bl, l, y, x, t) * d;
-      acc = fmaf(wd, d, acc);
-      gs += wd;
+      const float* t_row = target + (size_t)l * bl.C * HW + row;
+      float t[kIdentU];
+#pragma unroll
+      for (int k = 0; k < kIdentU; ++k) {
+        const int x = x0 + k * 256 + threadIdx.x;
+        t[k] = x < W ? __ldg(&t_row[x]) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < kIdentU; ++k) {
+        const int x = x0 + k * 256 + threadIdx.x;
+        if (x >= W) continue;
+        const float d = fmaf(u[k].x, u[k].x, u[k].y * u[k].y) - t[k];
+        const float wd = loss_weight(bl, l, y, x, t[k]) * d;
+        acc = fmaf(wd, d, acc);
+        gs[k] += wd;
+      }
     }
-    if (want_grad) u_row[x] = cscale(u, gscale * gs);
+    if (want_grad) {
+#pragma unroll
+      for (int k = 0; k < kIdentU; ++k) {
+        const int x = x0 + k * 256 + threadIdx.x;
+        if (x < W) u_row[x] = cscale(u[k], gscale * gs[k]);
+      }
+    }
   }
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;

@@ -36,6 +36,7 @@ constexpr int KC = 16;          // channels per staged chunk (one k16 step per t
 constexpr int PS = 24;          // bf16 per staged position / weight row: 48-byte rows, 16-byte
                                 // aligned for ldmatrix, consecutive rows on different banks
 constexpr int kThreads = 256;
+constexpr int kSU = 8;          // staged elements per thread per round (their loads in flight)
 constexpr int GS = TH * TW + 8; // bf16 per staged row of the weight-gradient tiles (272 bytes)
 
 enum { MODE_FWD = 0, MODE_DGRAD = 1 };
@@ -124,38 +125,70 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
 
   for (int c0 = 0; c0 < a.Kc; c0 += KC) {
     __syncthreads();  // the previous chunk's fragments have been loaded
-    // weights of this chunk: wt[tap][n][c] = W(n0 + n, c0 + c, tap)
-    for (int e = threadIdx.x; e < 9 * NT * KC; e += kThreads) {
-      const int c = e % KC, n = (e / KC) % NT, tap = e / (KC * NT);
-      const int nn = n0 + n, cc = c0 + c;
-      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-      if (nn < a.Nc && cc < a.Kc) {
-        if (MODE == MODE_FWD) v = a.w[((size_t)nn * a.Kc + cc) * 9 + tap];
-        else v = a.w[((size_t)cc * a.Nc + nn) * 9 + (8 - tap)];  // transposed, flipped
+    // weights of this chunk: wt[tap][n][c] = W(n0 + n, c0 + c, tap).  Element order makes
+    // consecutive threads read consecutive weights; kSU loads are in flight per thread.
+    for (int e0 = threadIdx.x; e0 < 9 * NT * KC; e0 += kSU * kThreads) {
+      __nv_bfloat16 v[kSU];
+      int dst[kSU];
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        int n, c, tap;
+        if (MODE == MODE_FWD) {  // e = (n * KC + c) * 9 + tap: w[n][c0 + c][tap] contiguous
+          tap = e % 9; c = (e / 9) % KC; n = e / (9 * KC);
+        } else {                 // e = (c * NT + n) * 9 + tap: w[c0 + c][n][8 - tap] contiguous
+          tap = e % 9; n = (e / 9) % NT; c = e / (9 * NT);
+        }
+        const int nn = n0 + n, cc = c0 + c;
+        v[u] = __float2bfloat16_rn(0.f);
+        dst[u] = -1;
+        if (e < 9 * NT * KC) {
+          dst[u] = (tap * NT + n) * PS + c;
+          if (nn < a.Nc && cc < a.Kc)
+            v[u] = MODE == MODE_FWD ? a.w[((size_t)nn * a.Kc + cc) * 9 + tap]
+                                    : a.w[((size_t)cc * a.Nc + nn) * 9 + (8 - tap)];
+        }
       }
-      wt[(tap * NT + n) * PS + c] = v;
+#pragma unroll
+      for (int u = 0; u < kSU; ++u)
+        if (dst[u] >= 0) wt[dst[u]] = v[u];
     }
     // the input patch of this chunk, channel-innermost
-    for (int e = threadIdx.x; e < KC * npos; e += kThreads) {
-      const int pos = e % npos, c = e / npos, cc = c0 + c;
-      const int Y = iy0 + pos / PW, X = ix0 + pos % PW;
-      if (MODE == MODE_FWD) {
-        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-        if (cc < a.Kc && Y >= 0 && Y < a.Hin && X >= 0 && X < a.Win)
-          v = a.x[(((size_t)b * a.Kc + cc) * a.Hin + Y) * a.Win + X];
-        patch[pos * PS + c] = v;
-      } else {
-        float g = 0.f;
-        if (cc < a.Kc && Y >= 0 && X >= 0 && Y % a.up == 0 && X % a.up == 0) {
-          const int gy = Y / a.up, gx = X / a.up;
-          if (gy < a.Hg && gx < a.Wg)
-            g = grad_in(a.dy, a.y, a.y_f32, a.relu,
-                        (((size_t)b * a.Kc + cc) * a.Hg + gy) * a.Wg + gx);
+    for (int e0 = threadIdx.x; e0 < KC * npos; e0 += kSU * kThreads) {
+      float g[kSU];
+      __nv_bfloat16 xv[kSU];
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        const int pos = e % npos, cc = c0 + e / npos;
+        const int Y = iy0 + pos / PW, X = ix0 + pos % PW;
+        g[u] = 0.f;
+        xv[u] = __float2bfloat16_rn(0.f);
+        if (e < KC * npos && cc < a.Kc) {
+          if (MODE == MODE_FWD) {
+            if (Y >= 0 && Y < a.Hin && X >= 0 && X < a.Win)
+              xv[u] = a.x[(((size_t)b * a.Kc + cc) * a.Hin + Y) * a.Win + X];
+          } else if (Y >= 0 && X >= 0 && Y % a.up == 0 && X % a.up == 0) {
+            const int gy = Y / a.up, gx = X / a.up;
+            if (gy < a.Hg && gx < a.Wg)
+              g[u] = grad_in(a.dy, a.y, a.y_f32, a.relu,
+                             (((size_t)b * a.Kc + cc) * a.Hg + gy) * a.Wg + gx);
+          }
         }
-        __nv_bfloat16 hi, lo;
-        split_bf16(g, hi, lo);
-        patch[pos * PS + c] = hi;
-        patch[(npos + pos) * PS + c] = lo;
+      }
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e >= KC * npos) continue;
+        const int pos = e % npos, c = e / npos;
+        if (MODE == MODE_FWD) {
+          patch[pos * PS + c] = xv[u];
+        } else {
+          __nv_bfloat16 hi, lo;
+          split_bf16(g[u], hi, lo);
+          patch[pos * PS + c] = hi;
+          patch[(npos + pos) * PS + c] = lo;
+        }
       }
     }
     __syncthreads();
@@ -216,7 +249,8 @@ struct WgradArgs {
 // dW partial sums of one CTA: co block blockIdx.y (64 channels), ci chunk blockIdx.z (16
 // channels x 9 taps), pixel tiles [blockIdx.x * per_cta, +per_cta).  Warp w: m16 block w & 3
 // (16 output channels), n8 blocks 9 (w >> 2) .. + 9 of the 18 (tap, ci) blocks.
-__global__ void __launch_bounds__(kThreads) k_conv_wgrad_tc(WgradArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_conv_wgrad_tc(WgradArgs a) {
+  constexpr int kSU = 4;  // two resident CTAs: fewer staged loads in flight per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* gs = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [2][NT][GS] g hi / lo
   __nv_bfloat16* xs = gs + 2 * NT * GS;                              // [9 * KC][GS] shifted x
@@ -232,42 +266,65 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad_tc(WgradArgs a) {
   for (int j = 0; j < 9; ++j)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-  float dbsum = 0.f;  // warp w: channels co0 + 8 w .. + 8 (lane & 7), lanes 0-7 hold them
+  __shared__ float sdb[NT];  // this CTA's bias-gradient partial sums (ci chunk 0 only)
+  if (threadIdx.x < NT) sdb[threadIdx.x] = 0.f;
   for (long long t = t0; t < t1; ++t) {
     const int b = (int)(t / ((long long)ntx * nty));
     const int r = (int)(t % ((long long)ntx * nty));
     const int oy0 = (r / ntx) * TH, ox0 = (r % ntx) * TW;
     __syncthreads();  // the previous tile's fragments have been loaded
-    for (int e = threadIdx.x; e < NT * TH * TW; e += kThreads) {
-      const int p = e % (TH * TW), co = e / (TH * TW);
-      const int oy = oy0 + p / TW, ox = ox0 + p % TW;
-      float g = 0.f;
-      if (co0 + co < a.CO && oy < a.Ho && ox < a.Wo)
-        g = grad_in(a.dy, a.y, a.y_f32, a.relu,
-                    (((size_t)b * a.CO + co0 + co) * a.Ho + oy) * a.Wo + ox);
-      __nv_bfloat16 hi, lo;
-      split_bf16(g, hi, lo);
-      gs[co * GS + p] = hi;
-      gs[(NT + co) * GS + p] = lo;
+    // g of 64 channels x 128 pixels; a warp's elements of one round share one channel, so
+    // the bias gradient is a warp sum per round (of the FP32 g, not of its split parts)
+    for (int e0 = threadIdx.x; e0 < NT * TH * TW; e0 += kSU * kThreads) {
+      float g[kSU];
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        const int p = e % (TH * TW), co = e / (TH * TW);
+        const int oy = oy0 + p / TW, ox = ox0 + p % TW;
+        g[u] = 0.f;
+        if (e < NT * TH * TW && co0 + co < a.CO && oy < a.Ho && ox < a.Wo)
+          g[u] = grad_in(a.dy, a.y, a.y_f32, a.relu,
+                         (((size_t)b * a.CO + co0 + co) * a.Ho + oy) * a.Wo + ox);
+      }
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e >= NT * TH * TW) continue;  // warp-uniform (the bound is a multiple of 32)
+        const int p = e % (TH * TW), co = e / (TH * TW);
+        __nv_bfloat16 hi, lo;
+        split_bf16(g[u], hi, lo);
+        gs[co * GS + p] = hi;
+        gs[(NT + co) * GS + p] = lo;
+        if (blockIdx.z == 0) {
+          float v = g[u];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) atomicAdd(&sdb[co], v);
+        }
+      }
     }
-    for (int e = threadIdx.x; e < 9 * KC * TH * TW; e += kThreads) {
-      const int p = e % (TH * TW), row = e / (TH * TW);  // row = tap * KC + ci
-      const int tap = row / KC, ci = ci0 + row % KC;
-      const int oy = oy0 + p / TW, ox = ox0 + p % TW;
-      const int iy = oy * a.stride + tap / 3 - 1, ix = ox * a.stride + tap % 3 - 1;
-      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-      if (ci < a.CI && oy < a.Ho && ox < a.Wo && iy >= 0 && iy < a.Hi && ix >= 0 && ix < a.Wi)
-        v = a.x[(((size_t)b * a.CI + ci) * a.Hi + iy) * a.Wi + ix];
-      xs[row * GS + p] = v;
+    for (int e0 = threadIdx.x; e0 < 9 * KC * TH * TW; e0 += kSU * kThreads) {
+      __nv_bfloat16 v[kSU];
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        const int p = e % (TH * TW), row = e / (TH * TW);  // row = tap * KC + ci
+        const int tap = row / KC, ci = ci0 + row % KC;
+        const int oy = oy0 + p / TW, ox = ox0 + p % TW;
+        const int iy = oy * a.stride + tap / 3 - 1, ix = ox * a.stride + tap % 3 - 1;
+        v[u] = __float2bfloat16_rn(0.f);
+        if (e < 9 * KC * TH * TW && ci < a.CI && oy < a.Ho && ox < a.Wo && iy >= 0 &&
+            iy < a.Hi && ix >= 0 && ix < a.Wi)
+          v[u] = a.x[(((size_t)b * a.CI + ci) * a.Hi + iy) * a.Wi + ix];
+      }
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e < 9 * KC * TH * TW) xs[(e / (TH * TW)) * GS + e % (TH * TW)] = v[u];
+      }
     }
     __syncthreads();
-    if (blockIdx.z == 0 && lane < 8) {  // bias gradient: FP32 sum of hi + lo
-      const int co = 8 * warp + lane;
-      float s = 0.f;
-      for (int p = 0; p < TH * TW; ++p)
-        s += __bfloat162float(gs[co * GS + p]) + __bfloat162float(gs[(NT + co) * GS + p]);
-      dbsum += s;
-    }
 #pragma unroll
     for (int ks = 0; ks < TH * TW / 16; ++ks) {
       uint32_t af[2][4];
@@ -308,8 +365,9 @@ __global__ void __launch_bounds__(kThreads) k_conv_wgrad_tc(WgradArgs a) {
       if (co < a.CO && ci < a.CI && acc[j][q] != 0.f)
         atomicAdd(&a.dw[((size_t)co * a.CI + ci) * 9 + tap], acc[j][q]);
     }
-  if (blockIdx.z == 0 && lane < 8 && co0 + 8 * warp + lane < a.CO && dbsum != 0.f)
-    atomicAdd(&a.db[co0 + 8 * warp + lane], dbsum);
+  __syncthreads();
+  if (blockIdx.z == 0 && threadIdx.x < NT && co0 + threadIdx.x < a.CO && sdb[threadIdx.x] != 0.f)
+    atomicAdd(&a.db[co0 + threadIdx.x], sdb[threadIdx.x]);
 }
 
 }  // namespace tc
