@@ -236,6 +236,111 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
     }
 }
 
+// Data gradient of a stride-2 convolution, one output parity class per CTA (blockIdx.z =
+// 2 py + px).  dx[2m + py][2n + px] gets W[co][ci][ky][kx] g[co][m + dy][n + dx] only from the
+// taps with ky = 1 (py = 0; dy = 0) or ky in {0, 2} (py = 1; dy = 1, 0), and likewise in x:
+// 1, 2, 2 or 4 taps, i.e. exactly the multiply-adds of the forward convolution, no zeros.
+// A CTA covers an 8 x 16 tile (m0, n0) of the g grid; the g patch (9 x 17 positions x 16
+// channels, hi and lo parts) and the class's weights are staged per 16-channel chunk.
+__global__ void __launch_bounds__(kThreads) k_conv_dgrad2_tc(ConvArgs a) {
+  constexpr int GH = TH + 1, GW = TW + 1;  // g positions of a tile plus the +1 taps
+  __shared__ __align__(16) __nv_bfloat16 wt[4 * NT * PS];        // [tap of the class][n][c]
+  __shared__ __align__(16) __nv_bfloat16 patch[2 * GH * GW * PS];  // [hi, lo][pos][c]
+  const int py = blockIdx.z >> 1, px = blockIdx.z & 1;
+  const int nty = py ? 2 : 1, ntx_ = px ? 2 : 1, ntap = nty * ntx_;
+  const int ntx = (a.Wg + TW - 1) / TW;
+  const int gx0 = (blockIdx.x % ntx) * TW, gy0 = (blockIdx.x / ntx) * TH;
+  const int nblk = (a.Nc + NT - 1) / NT;
+  const int b = blockIdx.y / nblk, n0 = (blockIdx.y % nblk) * NT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[NT / 8][4];
+#pragma unroll
+  for (int j = 0; j < NT / 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+  for (int c0 = 0; c0 < a.Kc; c0 += KC) {
+    __syncthreads();  // the previous chunk's fragments have been loaded
+    // class weights: wt[t][n][c] = W[c0 + c][n0 + n][ky_t][kx_t] (w[c][n][...] contiguous in n)
+    for (int e0 = threadIdx.x; e0 < ntap * NT * KC; e0 += kSU * kThreads) {
+      __nv_bfloat16 v[kSU];
+      int dst[kSU];
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        const int t = e % ntap, n = (e / ntap) % NT, c = e / (ntap * NT);
+        const int ky = py ? 2 * (t / ntx_) : 1, kx = px ? 2 * (t % ntx_) : 1;
+        const int nn = n0 + n, cc = c0 + c;
+        v[u] = __float2bfloat16_rn(0.f);
+        dst[u] = -1;
+        if (e < ntap * NT * KC) {
+          dst[u] = (t * NT + n) * PS + c;
+          if (nn < a.Nc && cc < a.Kc) v[u] = a.w[((size_t)cc * a.Nc + nn) * 9 + ky * 3 + kx];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kSU; ++u)
+        if (dst[u] >= 0) wt[dst[u]] = v[u];
+    }
+    for (int e0 = threadIdx.x; e0 < KC * GH * GW; e0 += kSU * kThreads) {
+      float g[kSU];
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        const int pos = e % (GH * GW), cc = c0 + e / (GH * GW);
+        const int gy = gy0 + pos / GW, gx = gx0 + pos % GW;
+        g[u] = 0.f;
+        if (e < KC * GH * GW && cc < a.Kc && gy < a.Hg && gx < a.Wg)
+          g[u] = grad_in(a.dy, a.y, a.y_f32, a.relu,
+                         (((size_t)b * a.Kc + cc) * a.Hg + gy) * a.Wg + gx);
+      }
+#pragma unroll
+      for (int u = 0; u < kSU; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e >= KC * GH * GW) continue;
+        const int pos = e % (GH * GW), c = e / (GH * GW);
+        __nv_bfloat16 hi, lo;
+        split_bf16(g[u], hi, lo);
+        patch[pos * PS + c] = hi;
+        patch[(GH * GW + pos) * PS + c] = lo;
+      }
+    }
+    __syncthreads();
+    const int arow = lane & 15, akh = lane >> 4;
+    const int bn = (lane & 7) + ((lane >> 4) << 3), bkh = (lane >> 3) & 1;
+    for (int t = 0; t < ntap; ++t) {
+      const int ky = py ? 2 * (t / ntx_) : 1, kx = px ? 2 * (t % ntx_) : 1;
+      const int dyo = (py + 1 - ky) >> 1, dxo = (px + 1 - kx) >> 1;  // 0 or 1
+      const int pos = (warp + dyo) * GW + arow + dxo;
+      uint32_t af[2][4];
+#pragma unroll
+      for (int part = 0; part < 2; ++part)
+        ldsm_x4(af[part], smem_u32(&patch[(part * GH * GW + pos) * PS + akh * 8]));
+#pragma unroll
+      for (int j = 0; j < NT / 16; ++j) {
+        uint32_t bf[4];
+        ldsm_x4(bf, smem_u32(&wt[(t * NT + 16 * j + bn) * PS + bkh * 8]));
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          mma_bf16(acc[2 * j], af[part], bf[0], bf[1]);
+          mma_bf16(acc[2 * j + 1], af[part], bf[2], bf[3]);
+        }
+      }
+    }
+  }
+  const int gq = lane >> 2, tq = lane & 3;
+  const int iy = 2 * (gy0 + warp) + py;
+  if (iy >= a.Hout) return;
+#pragma unroll
+  for (int j = 0; j < NT / 8; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = n0 + 8 * j + 2 * tq + (q & 1);
+      const int ix = 2 * (gx0 + gq + ((q >> 1) << 3)) + px;
+      if (n >= a.Nc || ix >= a.Wout) continue;
+      static_cast<float*>(a.out)[(((size_t)b * a.Nc + n) * a.Hout + iy) * a.Wout + ix] = acc[j][q];
+    }
+}
+
 struct WgradArgs {
   int B, CI, Hi, Wi, CO, Ho, Wo, stride, relu, y_f32;
   int per_cta;  // pixel tiles per CTA
@@ -422,7 +527,14 @@ cudaError_t conv3x3_dgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, 
   a.Hout = Hi; a.Wout = Wi; a.sc = 1; a.up = stride;
   a.relu = relu; a.y_f32 = y_f32; a.out_f32 = 1;
   a.dy = dy; a.y = y; a.w = (const __nv_bfloat16*)w; a.out = dx;
-  return launch_conv_tc<tc::MODE_DGRAD>(a, s);
+  if (stride == 1) return launch_conv_tc<tc::MODE_DGRAD>(a, s);
+  // stride 2: one launch over the four output parity classes
+  const int tiles = ((a.Hg + tc::TH - 1) / tc::TH) * ((a.Wg + tc::TW - 1) / tc::TW);
+  dim3 grid(tiles, B * ((a.Nc + tc::NT - 1) / tc::NT), 4);
+  prof_begin(KID_ENCODER, s);
+  tc::k_conv_dgrad2_tc<<<grid, tc::kThreads, 0, s>>>(a);
+  prof_end(KID_ENCODER, s);
+  return cudaGetLastError();
 }
 
 // Tensor-core weight and bias gradients (accumulated into dw, db with atomics).
