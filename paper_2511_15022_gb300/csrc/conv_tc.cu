@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
   const int b = blockIdx.y / nblk, n0 = (blockIdx.y % nblk) * NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int iy0 = oy0 * sc - 1, ix0 = ox0 * sc - 1;  // input position of patch (0, 0)
+  // 16-byte weight rows: w + (n Kc + c0) 9 is 16-byte aligned for every n when Kc % 8 == 0
+  const bool vec_w = (a.Kc % 8 == 0) && ((reinterpret_cast<uintptr_t>(a.w) & 15u) == 0);
 
   float acc[NT / 8][4];
 #pragma unroll
@@ -125,8 +127,22 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
 
   for (int c0 = 0; c0 < a.Kc; c0 += KC) {
     __syncthreads();  // the previous chunk's fragments have been loaded
-    // weights of this chunk: wt[tap][n][c] = W(n0 + n, c0 + c, tap).  Element order makes
-    // consecutive threads read consecutive weights; kSU loads are in flight per thread.
+    // weights of this chunk: wt[tap][n][c] = W(n0 + n, c0 + c, tap).  Forward weights of a
+    // full chunk are 144 consecutive BF16 per output channel: staged with 16-byte loads
+    // (when aligned), each scattered to its 8 (tap, channel) slots.
+    if (MODE == MODE_FWD && vec_w && c0 + KC <= a.Kc) {
+      for (int e = threadIdx.x; e < NT * 18; e += kThreads) {
+        const int n = e / 18, q = e % 18, nn = n0 + n;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (nn < a.Nc) v = __ldg(reinterpret_cast<const uint4*>(a.w + ((size_t)nn * a.Kc + c0) * 9) + q);
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int r = q * 8 + k;  // r = c * 9 + tap within the chunk
+          wt[((r % 9) * NT + n) * PS + r / 9] = h[k];
+        }
+      }
+    } else
     for (int e0 = threadIdx.x; e0 < 9 * NT * KC; e0 += kSU * kThreads) {
       __nv_bfloat16 v[kSU];
       int dst[kSU];
@@ -153,8 +169,13 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
       for (int u = 0; u < kSU; ++u)
         if (dst[u] >= 0) wt[dst[u]] = v[u];
     }
-    // the input patch of this chunk, channel-innermost
-    for (int e0 = threadIdx.x; e0 < KC * npos; e0 += kSU * kThreads) {
+    // the input patch of this chunk, channel-innermost (the chunk's real channels only; in a
+    // partial last chunk the slots beyond Kc are zeroed here, earlier chunks filled them)
+    const int kcr = min(KC, a.Kc - c0);
+    if (kcr < KC)
+      for (int e = threadIdx.x; e < npos * NPART; e += kThreads)
+        for (int c = kcr; c < KC; ++c) patch[e * PS + c] = __float2bfloat16_rn(0.f);
+    for (int e0 = threadIdx.x; e0 < kcr * npos; e0 += kSU * kThreads) {
       float g[kSU];
       __nv_bfloat16 xv[kSU];
 #pragma unroll
@@ -164,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
         const int Y = iy0 + pos / PW, X = ix0 + pos % PW;
         g[u] = 0.f;
         xv[u] = __float2bfloat16_rn(0.f);
-        if (e < KC * npos && cc < a.Kc) {
+        if (e < kcr * npos) {
           if (MODE == MODE_FWD) {
             if (Y >= 0 && Y < a.Hin && X >= 0 && X < a.Win)
               xv[u] = a.x[(((size_t)b * a.Kc + cc) * a.Hin + Y) * a.Win + X];
@@ -179,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_tc(ConvArgs a) {
 #pragma unroll
       for (int u = 0; u < kSU; ++u) {
         const int e = e0 + u * kThreads;
-        if (e >= KC * npos) continue;
+        if (e >= kcr * npos) continue;
         const int pos = e % npos, c = e / npos;
         if (MODE == MODE_FWD) {
           patch[pos * PS + c] = xv[u];
@@ -253,6 +274,8 @@ __global__ void __launch_bounds__(kThreads) k_conv_dgrad2_tc(ConvArgs a) {
   const int nblk = (a.Nc + NT - 1) / NT;
   const int b = blockIdx.y / nblk, n0 = (blockIdx.y % nblk) * NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // 16-byte weight rows: w + (c Nc + n0) 9 is 16-byte aligned when Nc % 8 == 0
+  const bool vec_w = (a.Nc % 8 == 0) && ((reinterpret_cast<uintptr_t>(a.w) & 15u) == 0);
   float acc[NT / 8][4];
 #pragma unroll
   for (int j = 0; j < NT / 8; ++j)
@@ -260,7 +283,24 @@ __global__ void __launch_bounds__(kThreads) k_conv_dgrad2_tc(ConvArgs a) {
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
   for (int c0 = 0; c0 < a.Kc; c0 += KC) {
     __syncthreads();  // the previous chunk's fragments have been loaded
-    // class weights: wt[t][n][c] = W[c0 + c][n0 + n][ky_t][kx_t] (w[c][n][...] contiguous in n)
+    // class weights: wt[t][n][c] = W[c0 + c][n0 + n][ky_t][kx_t].  For a full block of 64
+    // input channels, w[c][n0 .. n0 + 63][0 .. 8] is 576 consecutive BF16: 16-byte loads,
+    // each element kept if its tap belongs to the class.
+    if (vec_w && n0 + NT <= a.Nc && c0 + KC <= a.Kc) {
+      for (int e = threadIdx.x; e < KC * 72; e += kThreads) {
+        const int c = e / 72, q = e % 72, cc = c0 + c;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w + ((size_t)cc * a.Nc + n0) * 9) + q);
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int r = q * 8 + k, n = r / 9, tap = r % 9, ky = tap / 3, kx = tap % 3;
+          if ((py ? ky != 1 : ky == 1) && (px ? kx != 1 : kx == 1)) {
+            const int t = (py ? ky / 2 : 0) * ntx_ + (px ? kx / 2 : 0);
+            wt[(t * NT + n) * PS + c] = h[k];
+          }
+        }
+      }
+    } else
     for (int e0 = threadIdx.x; e0 < ntap * NT * KC; e0 += kSU * kThreads) {
       __nv_bfloat16 v[kSU];
       int dst[kSU];

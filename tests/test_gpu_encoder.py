@@ -46,6 +46,8 @@ CONV_CASES = [  # B, CI, H, W, CO, stride
     (1, 3, 130, 66, 32, 2),     # first layer, ragged tail of the 128-pixel CTAs
     (2, 128, 32, 32, 192, 2),   # last layer of the 512 x 512 encoder at 32 x 32 input
     (1, 1, 1, 1, 1, 2),         # one pixel
+    (1, 24, 20, 22, 72, 2),     # partial last channel chunk (24 = 16 + 8), partial 64-channel block
+    (2, 16, 18, 34, 64, 1),     # stride 1, exactly one chunk and one block
 ]
 
 
