@@ -274,8 +274,6 @@ __global__ void __launch_bounds__(kThreads) k_conv_dgrad2_tc(ConvArgs a) {
   const int nblk = (a.Nc + NT - 1) / NT;
   const int b = blockIdx.y / nblk, n0 = (blockIdx.y % nblk) * NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // 16-byte weight rows: w + (c Nc + n0) 9 is 16-byte aligned when Nc % 8 == 0
-  const bool vec_w = (a.Nc % 8 == 0) && ((reinterpret_cast<uintptr_t>(a.w) & 15u) == 0);
   float acc[NT / 8][4];
 #pragma unroll
   for (int j = 0; j < NT / 8; ++j)
@@ -283,24 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_dgrad2_tc(ConvArgs a) {
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
   for (int c0 = 0; c0 < a.Kc; c0 += KC) {
     __syncthreads();  // the previous chunk's fragments have been loaded
-    // class weights: wt[t][n][c] = W[c0 + c][n0 + n][ky_t][kx_t].  For a full block of 64
-    // input channels, w[c][n0 .. n0 + 63][0 .. 8] is 576 consecutive BF16: 16-byte loads,
-    // each element kept if its tap belongs to the class.
-    if (vec_w && n0 + NT <= a.Nc && c0 + KC <= a.Kc) {
-      for (int e = threadIdx.x; e < KC * 72; e += kThreads) {
-        const int c = e / 72, q = e % 72, cc = c0 + c;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.w + ((size_t)cc * a.Nc + n0) * 9) + q);
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int r = q * 8 + k, n = r / 9, tap = r % 9, ky = tap / 3, kx = tap % 3;
-          if ((py ? ky != 1 : ky == 1) && (px ? kx != 1 : kx == 1)) {
-            const int t = (py ? ky / 2 : 0) * ntx_ + (px ? kx / 2 : 0);
-            wt[(t * NT + n) * PS + c] = h[k];
-          }
-        }
-      }
-    } else
+    // class weights: wt[t][n][c] = W[c0 + c][n0 + n][ky_t][kx_t] (only the class's taps)
     for (int e0 = threadIdx.x; e0 < ntap * NT * KC; e0 += kSU * kThreads) {
       __nv_bfloat16 v[kSU];
       int dst[kSU];
@@ -413,6 +394,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_wgrad_tc(WgradArgs a) {
     for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
   __shared__ float sdb[NT];  // this CTA's bias-gradient partial sums (ci chunk 0 only)
   if (threadIdx.x < NT) sdb[threadIdx.x] = 0.f;
+  // rows of padding channels (co >= CO, ci >= CI) stay zero: cleared once, never restaged
+  const int cor = min(NT, a.CO - co0), cir = min(KC, a.CI - ci0);
+  for (int e = threadIdx.x; e < (NT - cor) * TH * TW; e += kThreads) {
+    const int co = cor + e / (TH * TW), p = e % (TH * TW);
+    gs[co * GS + p] = __float2bfloat16_rn(0.f);
+    gs[(NT + co) * GS + p] = __float2bfloat16_rn(0.f);
+  }
+  for (int e = threadIdx.x; e < 9 * (KC - cir) * TH * TW; e += kThreads) {
+    const int p = e % (TH * TW), r = e / (TH * TW), tap = r / (KC - cir), ci = cir + r % (KC - cir);
+    xs[(tap * KC + ci) * GS + p] = __float2bfloat16_rn(0.f);
+  }
   for (long long t = t0; t < t1; ++t) {
     const int b = (int)(t / ((long long)ntx * nty));
     const int r = (int)(t % ((long long)ntx * nty));
@@ -420,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_wgrad_tc(WgradArgs a) {
     __syncthreads();  // the previous tile's fragments have been loaded
     // g of 64 channels x 128 pixels; a warp's elements of one round share one channel, so
     // the bias gradient is a warp sum per round (of the FP32 g, not of its split parts)
-    for (int e0 = threadIdx.x; e0 < NT * TH * TW; e0 += kSU * kThreads) {
+    for (int e0 = threadIdx.x; e0 < cor * TH * TW; e0 += kSU * kThreads) {
       float g[kSU];
 #pragma unroll
       for (int u = 0; u < kSU; ++u) {
@@ -428,14 +420,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_wgrad_tc(WgradArgs a) {
         const int p = e % (TH * TW), co = e / (TH * TW);
         const int oy = oy0 + p / TW, ox = ox0 + p % TW;
         g[u] = 0.f;
-        if (e < NT * TH * TW && co0 + co < a.CO && oy < a.Ho && ox < a.Wo)
+        if (e < cor * TH * TW && oy < a.Ho && ox < a.Wo)
           g[u] = grad_in(a.dy, a.y, a.y_f32, a.relu,
                          (((size_t)b * a.CO + co0 + co) * a.Ho + oy) * a.Wo + ox);
       }
 #pragma unroll
       for (int u = 0; u < kSU; ++u) {
         const int e = e0 + u * kThreads;
-        if (e >= NT * TH * TW) continue;  // warp-uniform (the bound is a multiple of 32)
+        if (e >= cor * TH * TW) continue;  // warp-uniform (the bound is a multiple of 32)
         const int p = e % (TH * TW), co = e / (TH * TW);
         __nv_bfloat16 hi, lo;
         split_bf16(g[u], hi, lo);
@@ -449,25 +441,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_wgrad_tc(WgradArgs a) {
         }
       }
     }
-    for (int e0 = threadIdx.x; e0 < 9 * KC * TH * TW; e0 += kSU * kThreads) {
+    for (int e0 = threadIdx.x; e0 < 9 * cir * TH * TW; e0 += kSU * kThreads) {
       __nv_bfloat16 v[kSU];
+      int dst[kSU];
 #pragma unroll
       for (int u = 0; u < kSU; ++u) {
         const int e = e0 + u * kThreads;
-        const int p = e % (TH * TW), row = e / (TH * TW);  // row = tap * KC + ci
-        const int tap = row / KC, ci = ci0 + row % KC;
+        const int p = e % (TH * TW), r = e / (TH * TW);  // r = tap * cir + real channel
+        const int tap = r / cir, cl = r % cir, ci = ci0 + cl;
         const int oy = oy0 + p / TW, ox = ox0 + p % TW;
         const int iy = oy * a.stride + tap / 3 - 1, ix = ox * a.stride + tap % 3 - 1;
         v[u] = __float2bfloat16_rn(0.f);
-        if (e < 9 * KC * TH * TW && ci < a.CI && oy < a.Ho && ox < a.Wo && iy >= 0 &&
-            iy < a.Hi && ix >= 0 && ix < a.Wi)
+        dst[u] = e < 9 * cir * TH * TW ? (tap * KC + cl) * GS + p : -1;
+        if (dst[u] >= 0 && oy < a.Ho && ox < a.Wo && iy >= 0 && iy < a.Hi && ix >= 0 &&
+            ix < a.Wi)
           v[u] = a.x[(((size_t)b * a.CI + ci) * a.Hi + iy) * a.Wi + ix];
       }
 #pragma unroll
-      for (int u = 0; u < kSU; ++u) {
-        const int e = e0 + u * kThreads;
-        if (e < 9 * KC * TH * TW) xs[(e / (TH * TW)) * GS + e % (TH * TW)] = v[u];
-      }
+      for (int u = 0; u < kSU; ++u)
+        if (dst[u] >= 0) xs[dst[u]] = v[u];
     }
     __syncthreads();
 #pragma unroll
