@@ -448,7 +448,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_conv_wgrad_tc(WgradArgs a) {
       for (int u = 0; u < kSU; ++u) {
         const int e = e0 + u * kThreads;
         const int p = e % (TH * TW), r = e / (TH * TW);  // r = tap * cir + real channel
-        const int tap = r / cir, cl = r % cir, ci = ci0 + cl;
+        const int tap = cir == KC ? r / KC : r / cir;  // full chunks: constant divisor
+        const int cl = r - tap * cir, ci = ci0 + cl;
         const int oy = oy0 + p / TW, ox = ox0 + p % TW;
         const int iy = oy * a.stride + tap / 3 - 1, ix = ox * a.stride + tap % 3 - 1;
         v[u] = __float2bfloat16_rn(0.f);
