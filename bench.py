@@ -1077,6 +1077,32 @@ def learned_init_bench(dev, full: bool = False) -> dict:
 
 
 # ------------------------------------------------------------------ main
+def workload_config(w, mode: str, world: int) -> dict:
+    """The `config` object both arms print (the same keys and values for the same run)."""
+    return {"workload": w.name, "H": w.H, "W": w.W, "C": w.C, "L": w.L, "N": w.N,
+            "z_mm": [z * 1e3 for z in w.z_m], "pad": w.pad, "mode": mode,
+            "optimizer": "Adam (per-group lr)", "parallelism": f"replicas x{world}",
+            "l2": "working set ~0.5 GB > 129 MB L2 (inputs larger than L2)"}
+
+
+def oracle_full_steps(w, steps: int) -> dict:
+    """Whole FP64 oracle steps (forward + backward of the full workload, no sampling) timed on
+    the host cores."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_15022_gb300 import inputs
+    p64 = {k: v.astype(np.float64) for k, v in inputs.params_for(w).items()}
+    t64 = inputs.blob_targets(w.L, w.C, w.H, w.W).astype(np.float64)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.step(p64, t64, w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, w.pad, w.cutoff)
+        times.append(time.perf_counter() - t0)
+    return {"workload": w.name, "steps": steps, "s_per_step": statistics.median(times),
+            "cores": oracle.num_threads()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1090,6 +1116,10 @@ def main():
                     help="run the learned-initialiser extra on all 2000 targets")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-holograms and time-to-PSNR measurements")
+    ap.add_argument("--oracle-full-step", action="store_true",
+                    help="time one whole FP64 oracle step of the 1080p workload (minutes of "
+                         "host work) next to the sampled estimate of the reference arm, print "
+                         "one JSON line and exit")
 
     args = ap.parse_args()
 
@@ -1104,6 +1134,20 @@ def main():
 
     from paper_2511_15022_gb300 import inputs
     w = inputs.hd_1080p()
+
+    if args.oracle_full_step:
+        import oracle
+        oracle.build()
+        params_np = inputs.params_for(w)
+        target_np = inputs.blob_targets(w.L, w.C, w.H, w.W)
+        est = oracle_sample(w, params_np, target_np, 4.0, prop_scale_measured(w, 4.0))
+        full = oracle_full_steps(w, 1)
+        print(json.dumps({"what": "one whole FP64 oracle step against the sampled estimate",
+                          "full": full, "estimate_s_per_step": 1.0 / est["value"],
+                          "estimate_sample": est["sample"],
+                          "measured_over_estimate": full["s_per_step"] * est["value"]}),
+              flush=True)
+        return
 
     if args.impl == "reference":
         # The reference arm is the FP64 oracle on the host cores (rank 0 only).
@@ -1128,10 +1172,13 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": w.name, "H": w.H, "W": w.W, "C": w.C, "L": w.L, "N": w.N},
+                "config": workload_config(w, args.mode, world),
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                                  "sample": r["sample"]},
-                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                # the small parity workload (256 x 256, 2048 Gaussians, one plane) in whole
+                # oracle steps, no sampling: the oracle's own speed, measured
+                "small_workload_full_steps": oracle_full_steps(inputs.small_256(), 3)}
         print(json.dumps(line), flush=True)
         return
 
@@ -1321,12 +1368,8 @@ def main():
             "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Gaussians, blob targets)",
-            "config": {"workload": w.name, "H": w.H, "W": w.W, "C": w.C, "L": w.L, "N": w.N,
-                       "z_mm": [z * 1e3 for z in w.z_m], "pad": w.pad, "mode": args.mode,
-                       "optimizer": "Adam (per-group lr)", "parallelism": f"replicas x{world}",
-                       "l2": "working set ~0.5 GB > 129 MB L2 (inputs larger than L2)",
-                       "tuning": plan.get_tuning(),
-                       "identity_planes": list(plan.identity_planes)},
+            "config": workload_config(w, args.mode, world),
+            "plan": {"tuning": plan.get_tuning(), "identity_planes": list(plan.identity_planes)},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},

@@ -23,6 +23,13 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "1080x1920-C3-L3-N200k"
+    # both arms print the same config object for the same run
+    import bench
+    from paper_2511_15022_gb300 import inputs
+    assert d["config"] == json.loads(json.dumps(bench.workload_config(inputs.hd_1080p(),
+                                                                       "autograd", 1)))
+    small = d["small_workload_full_steps"]
+    assert small["workload"] == "small-256x256-C1-L1-N2048" and small["s_per_step"] > 0
 
 
 def test_work_model_matches_the_fused_pass_count():
