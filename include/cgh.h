@@ -320,6 +320,32 @@ cgh_status cgh_batch_bind(cgh_batch* batch, int32_t index, const cgh_params* par
 cgh_status cgh_batch_step(cgh_batch* batch, int32_t use_graph, void* stream);
 int64_t cgh_batch_kernels_per_step(const cgh_batch* batch);
 
+/* The same batched step as ONE persistent kernel launch (cooperative: every CTA resident):
+ * its phases -- clear, preprocess, tile scan and emit, raster forward, row pass,
+ * identity-plane loss, column pass, loss row pass, adjoint column pass, crop row pass, raster
+ * backward, gradient finalize and loss -- run for all holograms at once, the CTAs drawing
+ * (hologram, Gaussian block / tile / row / column) items from an atomic work queue, with a
+ * grid barrier between phases.  Same results as cgh_batch_step (the FFT passes are the
+ * generic runtime-length ones, one row or column per item).  The first call after a bind
+ * builds the descriptors (a small device allocation owned by the batch).  Each barrier wait is
+ * bounded (about one second of clock cycles): if it runs out, the kernel sets an error word
+ * and returns instead of hanging, and cgh_batch_persistent_status reports it. */
+cgh_status cgh_batch_step_persistent(cgh_batch* batch, void* stream);
+
+/* Synchronous read (blocks on `stream`) of the last persistent step's error word:
+ * *timed_out = 1 and CGH_ERR_TIMEOUT if a grid-barrier wait ran out, else 0 and CGH_OK. */
+cgh_status cgh_batch_persistent_status(cgh_batch* batch, int32_t* timed_out, void* stream);
+
+/* Test hook of the bounded barrier: with skip_barrier >= 0, CTA 0 of the next persistent
+ * steps does not arrive at grid barrier `skip_barrier` (0 = the one after the first phase),
+ * so that barrier can never complete and every CTA's wait runs out; timeout_s > 0 sets the
+ * wait budget in seconds of SM clock (<= 0: the default of about one second).
+ * skip_barrier = -1 restores normal operation. */
+cgh_status cgh_batch_persistent_test(cgh_batch* batch, int32_t skip_barrier, double timeout_s);
+
+/* CTAs of the persistent launch (all resident at once), 0 before the first persistent step. */
+int32_t cgh_batch_persistent_grid(const cgh_batch* batch);
+
 /* Autotuner: runs cgh_step `iters` times (after one warm-up) for every valid combination of
  * column block {1,2,4,8} x row block {1,2,3,4,8} x FFT kernel family {specialised, generic}
  * on the given data, keeps the fastest on the plan and writes it to best_out (may be NULL).

@@ -55,6 +55,8 @@ EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
            "cgh_intensity", "cgh_intensity_bwd", "cgh_plan_identity_planes",
+           "cgh_batch_step_persistent", "cgh_batch_persistent_status", "cgh_batch_persistent_test",
+           "cgh_batch_persistent_grid",
            "cgh_step", "cgh_step_scaled", "cgh_adam_step", "cgh_launch_count", "cgh_last_error_string",
            "cgh_profile_enable", "cgh_profile_collect", "cgh_kernel_count", "cgh_kernel_name",
            "cgh_raster_fwd_noalloc", "cgh_adam_step_table", "cgh_batch_create",
@@ -113,6 +115,11 @@ def load(build_if_missing: bool = True):
     lib.cgh_batch_step.argtypes = [vp, i32, vp]
     lib.cgh_batch_kernels_per_step.argtypes = [vp]
     lib.cgh_batch_kernels_per_step.restype = i64
+    lib.cgh_batch_step_persistent.argtypes = [vp, vp]
+    lib.cgh_batch_persistent_status.argtypes = [vp, ctypes.POINTER(i32), vp]
+    lib.cgh_batch_persistent_test.argtypes = [vp, i32, f64]
+    lib.cgh_batch_persistent_grid.argtypes = [vp]
+    lib.cgh_batch_persistent_grid.restype = i32
     lib.cgh_autotune.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Grads), vp, i32,
                                  vp, ctypes.POINTER(_Tuning)]
     lib.cgh_conv3x3_fwd.argtypes = [i32, i32, i32, i32, i32, i32, vp, vp, vp, i32, vp, i32, vp]
@@ -141,7 +148,8 @@ def load(build_if_missing: bool = True):
     lib.cgh_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("cgh_launch_count", "cgh_last_error_string", "cgh_kernel_count",
-                        "cgh_kernel_name", "cgh_batch_kernels_per_step"):
+                        "cgh_kernel_name", "cgh_batch_kernels_per_step",
+                        "cgh_batch_persistent_grid"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -632,6 +640,31 @@ class Batch:
     @property
     def kernels_per_step(self) -> int:
         return int(_lib.cgh_batch_kernels_per_step(self._h))
+
+    def step_persistent(self, stream=None):
+        """cgh_batch_step_persistent: the whole batched step as one persistent launch."""
+        _check(_lib.cgh_batch_step_persistent(self._h, ctypes.c_void_p(_stream(stream))),
+               "cgh_batch_step_persistent")
+
+    def persistent_status(self, stream=None) -> bool:
+        """True if a grid-barrier wait of the last persistent step ran out (it then returned
+        early; its outputs are not valid)."""
+        t = ctypes.c_int32()
+        st = _lib.cgh_batch_persistent_status(self._h, ctypes.byref(t),
+                                              ctypes.c_void_p(_stream(stream)))
+        if st not in (0, 3):
+            _check(st, "cgh_batch_persistent_status")
+        return bool(t.value)
+
+    def persistent_test(self, skip_barrier: int = -1, timeout_s: float = 0.0):
+        """Test hook: CTA 0 skips its arrival at grid barrier `skip_barrier` (-1: off); the
+        barrier wait budget in seconds (<= 0: default)."""
+        _check(_lib.cgh_batch_persistent_test(self._h, int(skip_barrier), float(timeout_s)),
+               "cgh_batch_persistent_test")
+
+    @property
+    def persistent_grid(self) -> int:
+        return int(_lib.cgh_batch_persistent_grid(self._h))
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

@@ -37,6 +37,7 @@ struct cgh_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches_per_replay = 0;
+  PersistState* persist = nullptr;  // the persistent step's descriptors (persist.cu)
 };
 
 static void batch_release_graph(cgh_batch* b) {
@@ -78,6 +79,7 @@ extern "C" cgh_status cgh_batch_create(cgh_plan* const* plans, int32_t count, cg
 extern "C" cgh_status cgh_batch_destroy(cgh_batch* b) {
   if (!b) return CGH_OK;
   batch_release_graph(b);
+  persist_release(b->persist);
   for (auto s : b->streams)
     if (s) cudaStreamDestroy(s);
   for (auto ev : b->done)
@@ -99,6 +101,7 @@ extern "C" cgh_status cgh_batch_bind(cgh_batch* b, int32_t i, const cgh_params* 
   b->losses[i] = loss_out;
   b->bound[i] = 1;
   batch_release_graph(b);  // pointers changed: capture again on the next graph step
+  persist_invalidate(b->persist);  // ... and rebuild the persistent step's descriptors
   return CGH_OK;
 }
 
@@ -162,6 +165,46 @@ extern "C" cgh_status cgh_batch_step(cgh_batch* b, int32_t use_graph, void* stre
 
 extern "C" int64_t cgh_batch_kernels_per_step(const cgh_batch* b) {
   return b ? b->launches_per_replay : 0;
+}
+
+extern "C" cgh_status cgh_batch_step_persistent(cgh_batch* b, void* stream) {
+  if (!b) return cgh_record_error(CGH_ERR_ARG, "batch is NULL");
+  for (char x : b->bound)
+    if (!x) return cgh_record_error(CGH_ERR_ARG, "every hologram must be bound (cgh_batch_bind)");
+  cgh_status st = persist_prepare(&b->persist, b->plans.data(), b->params.data(), b->grads.data(),
+                                  b->targets.data(), b->losses.data(), (int)b->plans.size());
+  if (st != CGH_OK) return st;
+  return persist_launch(b->persist, (cudaStream_t)stream);
+}
+
+extern "C" cgh_status cgh_batch_persistent_status(cgh_batch* b, int32_t* timed_out, void* stream) {
+  if (!b) return cgh_record_error(CGH_ERR_ARG, "batch is NULL");
+  return persist_status(b->persist, timed_out, (cudaStream_t)stream);
+}
+
+extern "C" cgh_status cgh_batch_persistent_test(cgh_batch* b, int32_t skip_barrier,
+                                                double timeout_s) {
+  if (!b) return cgh_record_error(CGH_ERR_ARG, "batch is NULL");
+  if (!b->persist) {
+    cgh_status st = persist_prepare(&b->persist, b->plans.data(), b->params.data(),
+                                    b->grads.data(), b->targets.data(), b->losses.data(),
+                                    (int)b->plans.size());
+    if (st != CGH_OK) return st;
+  }
+  long long budget = 0;
+  if (timeout_s > 0.0) {
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    budget = (long long)(timeout_s * (khz > 0 ? khz : 2000000) * 1000.0);
+    if (budget < 1) budget = 1;
+  }
+  persist_set_test(b->persist, skip_barrier, budget);
+  return CGH_OK;
+}
+
+extern "C" int32_t cgh_batch_persistent_grid(const cgh_batch* b) {
+  return b ? persist_grid(b->persist) : 0;
 }
 
 // ------------------------------------------------------------------ autotuner

@@ -123,6 +123,8 @@ struct LaunchShape {
   int threads, maxb;
   bool ok;
 };
+// blasm.cu: shared-memory stride (float2) of one transform of length n in the generic passes
+int fft_smem_stride(int n);
 // blasm.cu: CTA shape for nb transforms of d held in `buffers` shared-memory buffers
 // (ok = false if no shape fits the thread or shared-memory limits)
 LaunchShape fft_shape(const cgh_plan* p, const FFTDesc& d, int nb, int buffers);
@@ -188,6 +190,17 @@ cudaError_t conv3x3_dgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, 
 cudaError_t conv3x3_wgrad_tc(int B, int CI, int Hi, int Wi, int CO, int stride, const void* x,
                              int relu, const void* y, int y_f32, const float* dy, float* dw,
                              float* db, cudaStream_t s);
+// persist.cu: the persistent batched step (state owned by a cgh_batch)
+struct PersistState;
+cgh_status persist_prepare(PersistState** ps, cgh_plan* const* plans, const cgh_params* prm,
+                           const cgh_grads* grads, const float* const* targets,
+                           float* const* losses, int count);
+cgh_status persist_launch(PersistState* ps, cudaStream_t s);
+cgh_status persist_status(PersistState* ps, int32_t* timed_out, cudaStream_t s);
+void persist_set_test(PersistState* ps, int skip_barrier, long long budget_cycles);
+void persist_invalidate(PersistState* ps);
+void persist_release(PersistState* ps);
+int persist_grid(const PersistState* ps);
 // api.cu
 cudaError_t launch_adam(const cgh_adam_group* groups, int n, int step, float b1, float b2,
                         float eps, cudaStream_t s);
@@ -202,7 +215,7 @@ enum KernelId {
   KID_PREPROCESS = 0, KID_SCAN_TILES, KID_EMIT, KID_RASTER_FWD, KID_RASTER_BWD,
   KID_GRAD_FINALIZE, KID_ROWS_PAD_FWD, KID_COLS_FWD_PLANES, KID_ROWS_LOSS,
   KID_COLS_BWD_PLANES, KID_ROWS_INV_CROP, KID_LOSS_POINTWISE, KID_LOSS_FINALIZE, KID_ADAM,
-  KID_ENCODER, KID_POH, KID_IDENT_LOSS, KID_COUNT
+  KID_ENCODER, KID_POH, KID_IDENT_LOSS, KID_PERSIST, KID_COUNT
 };
 // Bracket one kernel launch: records a CUDA event before and after it on its stream when
 // profiling is enabled; otherwise only the launch counter moves.
