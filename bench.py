@@ -790,13 +790,16 @@ def batched_bench(dev, steps: int, warmup: int) -> dict:
             groups.append((p[k], torch.zeros_like(p[k]), torch.zeros_like(p[k]), g[k], LRS[k]))
     adam = cgh.AdamTable(groups)
 
-    def run(use_graph, n):
+    def run(mode, n):
         for _ in range(n):
-            batch.step(use_graph=use_graph)
+            if mode == "persistent":
+                batch.step_persistent()
+            else:
+                batch.step(use_graph=mode == "graph")
             adam.step()
 
     out = {}
-    for mode in (True, False):
+    for mode in ("graph", "separate", "persistent"):
         run(mode, max(warmup, 3))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -804,12 +807,19 @@ def batched_bench(dev, steps: int, warmup: int) -> dict:
         run(mode, steps)
         e1.record()
         torch.cuda.synchronize()
-        out["graph" if mode else "separate"] = steps / (e0.elapsed_time(e1) / 1000.0)
+        out[mode] = steps / (e0.elapsed_time(e1) / 1000.0)
+    timed_out = batch.persistent_status()
     return {"holograms": len(ws), "it_per_s_graph": out["graph"],
             "it_per_s_separate_launches": out["separate"],
+            "it_per_s_persistent": out["persistent"],
             "speedup": out["graph"] / out["separate"],
+            "persistent_over_separate": out["persistent"] / out["separate"],
+            "persistent_timed_out": timed_out,
             "holograms_per_s_graph": out["graph"] * len(ws),
             "kernels_per_step": batch.kernels_per_step + 1,
+            "persistent_launch": {"kernels_per_step": 2, "ctas": batch.persistent_grid,
+                                  "what": "one cooperative launch for all holograms' fused "
+                                          "steps + one table-Adam launch"},
             "pixels_total": sum(w.H * w.W for w in ws), "gaussians_total": sum(w.N for w in ws),
             "note": "each step: every hologram's fused fwd+bwd, then one Adam over all groups"}
 
