@@ -263,10 +263,22 @@ __device__ void run_item(int ph, const Holo& h, int i, unsigned char* dsm) {
   }
 }
 
+// Copy `bytes` (a multiple of 4) from global to shared memory with the whole CTA.
+__device__ __forceinline__ void cta_copy(void* dst, const void* src, int bytes) {
+  const int* s = static_cast<const int*>(src);
+  int* d = static_cast<int*>(dst);
+  for (int k = threadIdx.x; k < bytes / 4; k += blockDim.x) d[k] = __ldcg(&s[k]);
+}
+
 template <int MAXB>
 __global__ void __launch_bounds__(kThreads) k_batch_persistent(Ctl c) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ int s_item;
+  // the current hologram's descriptor and plane maps, staged once per change of hologram so
+  // the items read them (sizes, transfer-function constants) from shared memory
+  __shared__ Holo s_holo;
+  __shared__ BlasmDev s_bl[2];
+  int cur = -1;
   for (int ph = 0; ph < PH_COUNT; ++ph) {
     if (ph > 0 && !grid_sync(c, ph - 1)) return;
     const int* off = c.offsets + ph * (c.nh + 1);
@@ -282,7 +294,19 @@ __global__ void __launch_bounds__(kThreads) k_batch_persistent(Ctl c) {
         const int mid = (lo + hi + 1) >> 1;
         if (off[mid] <= it) lo = mid; else hi = mid - 1;
       }
-      run_item<MAXB>(ph, c.holos[lo], it - off[lo], dsm);
+      if (lo != cur) {
+        cta_copy(&s_holo, &c.holos[lo], sizeof(Holo));
+        cta_copy(&s_bl[0], c.holos[lo].bl, sizeof(BlasmDev));
+        cta_copy(&s_bl[1], c.holos[lo].blp, sizeof(BlasmDev));
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          s_holo.bl = &s_bl[0];
+          s_holo.blp = &s_bl[1];
+        }
+        __syncthreads();
+        cur = lo;
+      }
+      run_item<MAXB>(ph, s_holo, it - off[lo], dsm);
       __syncthreads();  // the item's shared memory is free before the next item
     }
   }
