@@ -809,7 +809,23 @@ def batched_bench(dev, steps: int, warmup: int) -> dict:
         torch.cuda.synchronize()
         out[mode] = steps / (e0.elapsed_time(e1) / 1000.0)
     timed_out = batch.persistent_status()
+    persistent_ctas = batch.persistent_grid
+    # context for the persistent form, which runs the generic FFT passes: the graph form with
+    # every plan on the generic passes too (rebinding recaptures the graph)
+    for plan in plans:
+        plan.set_tuning(fft_kernels=2)
+    for i, args in sorted(batch._keep.items()):
+        batch.bind(i, args[0], args[1], args[2], args[3])
+    run("graph", max(warmup, 3))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run("graph", steps)
+    e1.record()
+    torch.cuda.synchronize()
+    out["graph_generic"] = steps / (e0.elapsed_time(e1) / 1000.0)
     return {"holograms": len(ws), "it_per_s_graph": out["graph"],
+            "it_per_s_graph_generic_fft": out["graph_generic"],
             "it_per_s_separate_launches": out["separate"],
             "it_per_s_persistent": out["persistent"],
             "speedup": out["graph"] / out["separate"],
@@ -817,7 +833,7 @@ def batched_bench(dev, steps: int, warmup: int) -> dict:
             "persistent_timed_out": timed_out,
             "holograms_per_s_graph": out["graph"] * len(ws),
             "kernels_per_step": batch.kernels_per_step + 1,
-            "persistent_launch": {"kernels_per_step": 2, "ctas": batch.persistent_grid,
+            "persistent_launch": {"kernels_per_step": 2, "ctas": persistent_ctas,
                                   "what": "one cooperative launch for all holograms' fused "
                                           "steps + one table-Adam launch"},
             "pixels_total": sum(w.H * w.W for w in ws), "gaussians_total": sum(w.N for w in ws),
