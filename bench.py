@@ -1103,6 +1103,60 @@ def learned_init_bench(dev, full: bool = False) -> dict:
 
 
 # ------------------------------------------------------------------ main
+def encoder_step_bench(dev, steps: int = 20) -> dict:
+    """The learned initialiser's network on its workload batch (16 RGB 512 x 512 targets):
+    per-layer times of the tensor-core convolutions (forward; weight gradient; data + weight
+    gradient) and the whole training step (encoder forward, decode, the 16 holograms' fused
+    steps, parameter loss, decode adjoint, encoder backward, Adam), CUDA events."""
+    import torch
+
+    from paper_2511_15022_gb300 import cgh
+    from paper_2511_15022_gb300 import encoder as E
+    B, H = 16, 512
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    enc = E.Encoder(C=3, S=16, device=dev)
+    x = torch.rand(B, 3, H, H, device=dev)
+    _, acts = enc.forward(x)
+    layers = []
+    for i in range(enc.n_layers):
+        last = i == enc.n_layers - 1
+        xi, yi = acts[i], acts[i + 1]
+        dy = torch.randn(yi.shape, device=dev)
+        flop = 2.0 * B * yi.shape[-1] * yi.shape[-2] * enc.chans[i] * enc.chans[i + 1] * 9
+        f = timed(lambda: cgh.conv3x3_fwd(xi, enc.wb[i], enc.b[i], 2, relu=not last,
+                                          out_f32=last), steps)
+        wg = timed(lambda: cgh.conv3x3_bwd(xi, enc.wb[i], yi, dy, 2, relu=not last,
+                                           want_dx=False, dw=enc.dw[i], db=enc.db[i]), steps)
+        bw = timed(lambda: cgh.conv3x3_bwd(xi, enc.wb[i], yi, dy, 2, relu=not last,
+                                           want_dx=i > 0, dw=enc.dw[i], db=enc.db[i]), steps)
+        layers.append({"layer": i, "channels": [enc.chans[i], enc.chans[i + 1]],
+                       "input": [xi.shape[-2], xi.shape[-1]], "fwd_ms": round(f, 4),
+                       "fwd_tflops": round(flop / f / 1e9, 1), "wgrad_ms": round(wg, 4),
+                       "bwd_ms": round(bw, 4)})
+    pipe = E.Pipeline(H, H, (638e-9, 520e-9, 450e-9), 8e-6, 5e-3, chunk=50, train_batch=B,
+                      device=dev, seed=0)
+    T = torch.rand(64, 3, H, H, device=dev) * 0.7
+    data = pipe.enc.anchors(64, H, H)
+    step_ms = timed(lambda: pipe.train(T, data, 1), steps)
+    pipe.close()
+    return {"batch": B, "image": [H, H], "layers": layers,
+            "forward_ms": round(sum(l["fwd_ms"] for l in layers), 3),
+            "backward_ms": round(sum(l["bwd_ms"] for l in layers), 3),
+            "training_step_ms": round(step_ms, 3),
+            "what": "mma.sync m16n8k16 BF16 implicit-GEMM convolutions, FP32 accumulation"}
+
+
 def workload_config(w, mode: str, world: int) -> dict:
     """The `config` object both arms print (the same keys and values for the same run)."""
     return {"workload": w.name, "H": w.H, "W": w.W, "C": w.C, "L": w.L, "N": w.N,
@@ -1142,6 +1196,9 @@ def main():
                     help="run the learned-initialiser extra on all 2000 targets")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-holograms and time-to-PSNR measurements")
+    ap.add_argument("--encoder-step", action="store_true",
+                    help="time the learned initialiser's convolutions and training step only, "
+                         "print one JSON line and exit")
     ap.add_argument("--oracle-full-step", action="store_true",
                     help="time one whole FP64 oracle step of the 1080p workload (minutes of "
                          "host work) next to the sampled estimate of the reference arm, print "
@@ -1160,6 +1217,13 @@ def main():
 
     from paper_2511_15022_gb300 import inputs
     w = inputs.hd_1080p()
+
+    if args.encoder_step:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        print(json.dumps(encoder_step_bench(dev)), flush=True)
+        return
 
     if args.oracle_full_step:
         import oracle
@@ -1417,6 +1481,7 @@ def main():
             line["time_to_psnr"] = time_to_psnr(dev, plan_tuning=tuned)
             line["time_to_psnr_adan"] = time_to_psnr(dev, plan_tuning=tuned, optimizer="adan")
             line["learned_init"] = learned_init_bench(dev, full=args.learned_full)
+            line["encoder_step"] = encoder_step_bench(dev)
             line["stress_4k"] = stress_4k(dev)
             line["render_sweep"] = render_sweep(dev)
             line["resolution_sweep"] = resolution_sweep(dev)
