@@ -200,8 +200,8 @@ class ClockSampler:
 
 
 FFT_SOURCES = ("fft.cuh", "fftreg.cuh", "blasm_common.cuh", "blasm_reg.cuh", "blasm_spec.h",
-               "blasm_spec_*.cu", "blasm.cu", "cgh_internal.h")
-RASTER_SOURCES = ("raster.cu", "cgh_internal.h")
+               "blasm_spec_*.cu", "blasm.cu", "blasm_generic.cuh", "cgh_internal.h")
+RASTER_SOURCES = ("raster.cu", "raster.cuh", "cgh_internal.h")
 
 
 def kernel_source_sha(kernel: str = "") -> str:
