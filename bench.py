@@ -935,7 +935,8 @@ def batched_time_to_psnr(dev, it_per_s_separate: float, iters: int = 400,
 
 # ------------------------------------------------------------------ time to target PSNR
 def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_every: int = 10,
-                 plan_tuning=None, optimizer: str = "adam") -> dict:
+                 plan_tuning=None, optimizer: str = "adam", cutoff=None,
+                 anneal_all: float = 0.0) -> dict:
     """Plain method (random initialisation, Adam with the paper's per-group learning rates,
     position rate cosine-annealed 1e-2 -> 1e-3) on a planted target: seed-999 Gaussians of
     the same distributions rendered and propagated by this library, amplitudes scaled so the
@@ -943,7 +944,9 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
     optimum of the loss.  Reports wall time and iterations until the plane-mean PSNR
     (predicted and target intensities clipped to [0, 1]) first reaches 25, 27, 28 and
     target_db (the run stops there or after max_iters).  PSNR checks are outside the timed
-    optimisation."""
+    optimisation.  cutoff overrides the skip threshold of both the planted target and the fit
+    (0: smooth mode); anneal_all > 0 also cosine-anneals every other group's rate from its
+    paper value to anneal_all times it over the run."""
     import math
 
     import torch
@@ -951,8 +954,8 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
     from paper_2511_15022_gb300 import cgh, inputs
     from paper_2511_15022_gb300.autograd import hologram_loss
     w = inputs.hd_1080p()
-    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m, cutoff=w.cutoff,
-                    max_gaussians=w.N, device=dev)
+    plan = cgh.Plan(w.H, w.W, w.wavelengths_m, w.pitch_m, w.z_m,
+                    cutoff=w.cutoff if cutoff is None else cutoff, max_gaussians=w.N, device=dev)
     if plan_tuning:
         plan.set_tuning(**{k: v for k, v in plan_tuning.items() if k != "pair_capacity_per_gaussian"})
     # structured (image-like) planted field: zero phases, per-channel amplitudes read from a
@@ -973,19 +976,21 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
 
     elapsed, it, hist = 0.0, 0, [(0, round(psnr(), 2))]
     reached = None
-    levels = (25.0, 27.0, 28.0, target_db)
+    levels = tuple(sorted({25.0, 27.0, 28.0, 29.0, 30.0, target_db}))
     crossed = {}
     while it < max_iters:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(check_every):
             it += 1
-            lr_pos = 1e-3 + 0.5 * (1e-2 - 1e-3) * (1 + math.cos(math.pi * it / max_iters))
+            cos = 0.5 * (1 + math.cos(math.pi * it / max_iters))
+            lr_pos = 1e-3 + (1e-2 - 1e-3) * cos
+            other = (anneal_all + (1.0 - anneal_all) * cos) if anneal_all > 0 else 1.0
             for k in params:
                 params[k].grad = None
             hologram_loss(plan, params, target).backward()
-            groups = [(params[k].data, params[k].grad, *state[k], lr_pos if k == "xy_raw" else LRS[k])
-                      for k in cgh.PARAM_KEYS]
+            groups = [(params[k].data, params[k].grad, *state[k],
+                       lr_pos if k == "xy_raw" else LRS[k] * other) for k in cgh.PARAM_KEYS]
             if optimizer == "adan":
                 cgh.adan_step(groups, it)
             else:
@@ -1007,6 +1012,7 @@ def time_to_psnr(dev, target_db: float = 30.0, max_iters: int = 3000, check_ever
             "levels": {str(l): crossed.get(l) for l in levels},
             "iterations_run": it, "seconds_run": elapsed, "psnr_history": hist[::4] + hist[-1:],
             "method": f"plain (random init), autograd recompute path, {optimizer.capitalize()}",
+            "cutoff": w.cutoff if cutoff is None else cutoff, "anneal_all": anneal_all,
             "initial_db": hist[0][1],
             "target": ("planted: seed-999 Gaussians, zero phases, amplitudes from a smooth blob "
                        "image, rendered and propagated; mean intensity 0.35, PSNR on [0, 1]-clipped "
@@ -1196,6 +1202,9 @@ def main():
                     help="run the learned-initialiser extra on all 2000 targets")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-holograms and time-to-PSNR measurements")
+    ap.add_argument("--psnr-study", action="store_true",
+                    help="time to PSNR on the 1080p planted target under longer schedules, "
+                         "annealed rates and without the opacity cutoff; one JSON line, exit")
     ap.add_argument("--encoder-step", action="store_true",
                     help="time the learned initialiser's convolutions and training step only, "
                          "print one JSON line and exit")
@@ -1217,6 +1226,23 @@ def main():
 
     from paper_2511_15022_gb300 import inputs
     w = inputs.hd_1080p()
+
+    if args.psnr_study:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        runs = {"paper_schedule_3000": dict(max_iters=3000),
+                "paper_schedule_9000": dict(max_iters=9000),
+                "smooth_mode_3000": dict(max_iters=3000, cutoff=0.0),
+                "all_rates_annealed_to_1pct_6000": dict(max_iters=6000, anneal_all=0.01)}
+        out = {}
+        for name, kw in runs.items():
+            r = time_to_psnr(dev, target_db=35.0, check_every=25, **kw)
+            out[name] = {k: r[k] for k in ("best_db", "final_db", "levels", "iterations_run",
+                                           "seconds_run", "cutoff", "anneal_all")}
+            out[name]["psnr_history"] = r["psnr_history"][::3]
+        print(json.dumps(out), flush=True)
+        return
 
     if args.encoder_step:
         import torch
