@@ -142,14 +142,25 @@ cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* 
   const int* ts = (const int*)(p->ws + p->off_tile_start);
   const int* pairs = (const int*)(p->ws + p->off_pairs);
   const int nblk = (prm->N + 255) / 256;
+  // one CTA per 32 x 32 region of 2 x 2 tiles
+  dim3 rgrid((p->tiles_x + 1) / 2, (p->tiles_y + 1) / 2);
+  const size_t rsmem = raster_bwd_region_smem(p->C);
+  switch (p->C) {
+    case 1: e = cudaFuncSetAttribute(k_raster_bwd_region<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem); break;
+    case 2: e = cudaFuncSetAttribute(k_raster_bwd_region<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem); break;
+    case 3: e = cudaFuncSetAttribute(k_raster_bwd_region<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem); break;
+    default: e = cudaFuncSetAttribute(k_raster_bwd_region<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem); break;
+  }
+  if (e != cudaSuccess) return e;
   prof_begin(KID_RASTER_BWD, s);
   switch (p->C) {
-    case 1: k_raster_bwd<1><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
-    case 2: k_raster_bwd<2><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
-    case 3: k_raster_bwd<3><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
-    default: k_raster_bwd<4><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    case 1: k_raster_bwd_region<1><<<rgrid, 256, rsmem, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    case 2: k_raster_bwd_region<2><<<rgrid, 256, rsmem, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    case 3: k_raster_bwd_region<3><<<rgrid, 256, rsmem, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
+    default: k_raster_bwd_region<4><<<rgrid, 256, rsmem, s>>>(rc, rec, rect, ts, pairs, dU, raw); break;
   }
   prof_end(KID_RASTER_BWD, s);
+  (void)grid;
   if (prm->N > 0) {
     prof_begin(KID_GRAD_FINALIZE, s);
     switch (p->C) {

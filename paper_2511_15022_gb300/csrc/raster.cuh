@@ -573,6 +573,161 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
 }
 #endif  // CGH_ITEMS_ONLY
 
+// Backward over a 32 x 32 region (2 x 2 tiles) per CTA of 256 threads: the region's dL/dU is
+// staged in shared memory; the CTA walks the lists of its four 16 x 16 tiles and keeps a
+// Gaussian only from its home tile -- the first of its tiles inside the region,
+// (max(r.x, 2 STX), max(r.y, 2 STY)) -- so every Gaussian meets the region once; each warp then
+// sweeps one kept Gaussian's box inside the region (up to 1024 pixels, flattened), with the
+// moments, reduction and atomics of raster_bwd_tile.  Compared with one CTA per tile, a
+// Gaussian that straddles tile borders is reduced once per region instead of once per tile.
+// Shared memory: srec[256 * CGH_REC_F4], sgid[256], sdu[C][1024], one int.
+constexpr int kSuper = 2 * CGH_TILE;
+template <int C>
+__device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
+                                                  const float4* __restrict__ rec,
+                                                  const int4* __restrict__ rect,
+                                                  const int* __restrict__ tile_start,
+                                                  const int* __restrict__ pairs,
+                                                  const float2* __restrict__ dU,
+                                                  float* __restrict__ raw, int STX, int STY,
+                                                  float4* srec, int* sgid,
+                                                  float2 (*sdu)[kSuper * kSuper], int* scount) {
+  constexpr int NV = 2 * C + 6;
+  constexpr int NVP = NV <= 8 ? 8 : 16;  // padded to a power of two for the reduce-scatter
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ox = STX * kSuper, oy = STY * kSuper;
+  {
+    const size_t plane = (size_t)rc.H * rc.W;
+    for (int i = threadIdx.x; i < kSuper * kSuper; i += blockDim.x) {
+      const int px = ox + (i & (kSuper - 1)), py = oy + i / kSuper;
+      const bool inside = px < rc.W && py < rc.H;
+      const size_t o = (size_t)py * rc.W + px;
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        sdu[c][i] = inside ? CGH_WS_LOAD(&dU[c * plane + o]) : make_float2(0.f, 0.f);
+    }
+  }
+  const float fox = (float)ox, foy = (float)oy;
+  for (int q = 0; q < 4; ++q) {
+    const int sx = 2 * STX + (q & 1), sy = 2 * STY + (q >> 1);
+    if (sx >= rc.tiles_x || sy >= rc.tiles_y) continue;  // CTA-uniform
+    const int tile = sy * rc.tiles_x + sx;
+    const int start = CGH_WS_LOAD(&tile_start[tile]), end = CGH_WS_LOAD(&tile_start[tile + 1]);
+    const bool exhaustive = (long long)end > rc.cap;
+    const int count = exhaustive ? rc.N : end - start;
+    for (int base = 0; base < count; base += 256) {
+      __syncthreads();  // the previous batch has been swept; dU is staged
+      if (threadIdx.x == 0) *scount = 0;
+      __syncthreads();
+      const int i = base + threadIdx.x;
+      int gid = 0;
+      bool keep = false;
+      if (i < count) {
+        gid = exhaustive ? i : CGH_WS_LOAD(&pairs[start + i]);
+        const int4 r = CGH_WS_LOAD(&rect[gid]);
+        keep = r.x <= sx && sx <= r.z && r.y <= sy && sy <= r.w &&
+               sx == max(r.x, 2 * STX) && sy == max(r.y, 2 * STY);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      int wbase = 0;
+      if (lane == 0 && bal) wbase = atomicAdd(scount, __popc(bal));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (keep) {
+        const int slot = wbase + __popc(bal & ((1u << lane) - 1u));
+        const float4* g = rec + (size_t)gid * CGH_REC_F4;
+#pragma unroll
+        for (int k = 0; k < CGH_REC_F4; ++k) srec[slot * CGH_REC_F4 + k] = CGH_WS_LOAD(&g[k]);
+        sgid[slot] = gid;
+      }
+      __syncthreads();
+      const int nb = *scount;
+      for (int j = warp; j < nb; j += 8) {
+        const float4 bb = srec[j * CGH_REC_F4 + 2];
+        // pixel box of the Gaussian inside this region (region coordinates)
+        const int x0 = (int)ceilf(fmaxf(bb.x, fox)) - ox;
+        const int x1 = (int)floorf(fminf(bb.y, fox + (float)(kSuper - 1))) - ox;
+        const int y0 = (int)ceilf(fmaxf(bb.z, foy)) - oy;
+        const int y1 = (int)floorf(fminf(bb.w, foy + (float)(kSuper - 1))) - oy;
+        if (x0 > x1 || y0 > y1) continue;  // warp-uniform
+        const float4 r0 = srec[j * CGH_REC_F4 + 0];
+        const float4 r1 = srec[j * CGH_REC_F4 + 1];
+        const float4 r3 = srec[j * CGH_REC_F4 + 3];
+        const float4 r4 = srec[j * CGH_REC_F4 + 4];
+        const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+        const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+        // flattened box pixels: floor(k / bw) from one FP32 product, exact here because
+        // k < 1024 and the fractional part of (k + 1/2) / bw stays at least 1/64 away from an
+        // integer (relative rounding of the product below 2^-23 * 1024)
+        const int bw = x1 - x0 + 1, npx = bw * (y1 - y0 + 1);
+        const float inv_bw = 1.f / (float)bw;
+        float acc[NVP];
+#pragma unroll
+        for (int v = 0; v < NVP; ++v) acc[v] = 0.f;
+        for (int k = lane; k < npx; k += 32) {
+          const int ry = (int)(((float)k + 0.5f) * inv_bw);
+          const int lx_ = x0 + (k - ry * bw), ly_ = y0 + ry;
+          const float dx = (float)(ox + lx_) - r0.x, dy = (float)(oy + ly_) - r0.y;
+          const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
+          if (p2 < r1.y) continue;
+          const int pix = ly_ * kSuper + lx_;
+          const float G = exp2f(fmaxf(p2, kP2Floor));
+          const float aG = r1.z * G;
+          const float a = fminf(kAlphaCap, aG);
+          float S = 0.f;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const float2 gv = sdu[c][pix];
+            acc[c] = fmaf(a, gv.x, acc[c]);
+            acc[C + c] = fmaf(a, gv.y, acc[C + c]);
+            S = fmaf(Ac[c], gv.x, fmaf(Bc[c], gv.y, S));
+          }
+          if (aG < kAlphaCap) {
+            acc[2 * C] = fmaf(S, G, acc[2 * C]);
+            if (p2 > kP2Floor) {
+              const float u = S * aG;
+              const float udx = u * dx, udy = u * dy;
+              acc[2 * C + 1] += udx;
+              acc[2 * C + 2] += udy;
+              acc[2 * C + 3] = fmaf(udx, dx, acc[2 * C + 3]);
+              acc[2 * C + 4] = fmaf(udx, dy, acc[2 * C + 4]);
+              acc[2 * C + 5] = fmaf(udy, dy, acc[2 * C + 5]);
+            }
+          }
+        }
+        int vidx = 0;
+        ReduceScatter<NVP, 16>::run(acc, lane, vidx);
+        if ((lane & (32 / NVP - 1)) == 0 && vidx < NV && acc[0] != 0.f)
+          atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
+      }
+    }
+  }
+}
+
+#ifndef CGH_ITEMS_ONLY
+template <int C>
+__global__ void __launch_bounds__(256) k_raster_bwd_region(RasterConsts rc,
+                                                           const float4* __restrict__ rec,
+                                                           const int4* __restrict__ rect,
+                                                           const int* __restrict__ tile_start,
+                                                           const int* __restrict__ pairs,
+                                                           const float2* __restrict__ dU,
+                                                           float* __restrict__ raw) {
+  extern __shared__ __align__(16) unsigned char smem_rb[];
+  float4* srec = reinterpret_cast<float4*>(smem_rb);
+  int* sgid = reinterpret_cast<int*>(srec + 256 * CGH_REC_F4);
+  float2(*sdu)[kSuper * kSuper] = reinterpret_cast<float2(*)[kSuper * kSuper]>(sgid + 256);
+  int* scount = reinterpret_cast<int*>(&sdu[C][0]);
+  raster_bwd_region<C>(rc, rec, rect, tile_start, pairs, dU, raw, blockIdx.x, blockIdx.y, srec,
+                       sgid, sdu, scount);
+}
+#endif  // CGH_ITEMS_ONLY
+
+// shared memory of k_raster_bwd_region<C>
+__host__ __device__ constexpr size_t raster_bwd_region_smem(int C) {
+  return sizeof(float4) * 256 * CGH_REC_F4 + sizeof(int) * 256 +
+         sizeof(float2) * (size_t)C * kSuper * kSuper + sizeof(int);
+}
+
 template <int C>
 __device__ __forceinline__ void grad_finalize_one(const RasterConsts& rc, const cgh_params& p,
                                                   const float* __restrict__ raw,
