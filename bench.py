@@ -36,23 +36,22 @@ def algorithmic_bytes(w, ident: int = 0) -> dict:
     """Compulsory HBM bytes per launch of each FFT-pass kernel: complex64 units of
     S = H*W*8 bytes per channel (pad / crop halves skipped, planes fused).  `ident` planes
     propagate by the identity (distance 0) and are taken in the pixel domain: they move no
-    column or loss-row bytes; their loss pass reads U(0) and their targets and writes the
-    seed, and the last row pass adds that seed (one more read).  rows_loss is the fused pass
-    with the gradient; the forward-only launch moves 2.5 units per plane instead of 4.5."""
+    column or loss-row bytes; the forward raster reads their targets as it finishes each pixel
+    and writes the seed, and the last row pass adds that seed (one more read).  rows_loss is
+    the fused pass with the gradient; the forward-only launch moves 2.5 units per plane
+    instead of 4.5."""
     S = w.H * w.W * 8
     C, Lp = w.C, w.L - ident
-    out = {
+    return {
         "k_rows_pad_fwd": (1 + 2) * C * S,
         "k_cols_fwd_planes": (2 + 2 * Lp) * C * S,
         "k_rows_loss": (2 + 0.5 + 2) * Lp * C * S,
         "k_cols_bwd_planes": (2 * Lp + 2) * C * S,
         "k_rows_inv_crop": (2 + 1 + (1 if ident else 0)) * C * S,
-        "k_raster_fwd": 1 * C * S,
+        # the launch with the gradient: U(0), and with identity planes their targets and seed
+        "k_raster_fwd": (1 + (0.5 * ident + 1 if ident else 0)) * C * S,
         "k_raster_bwd": 1 * C * S,
     }
-    if ident:
-        out["k_ident_loss"] = (2 + 0.5 * ident) * C * S
-    return out
 
 
 def raster_pairs(p: dict, cutoff: float) -> float:
@@ -79,7 +78,8 @@ def step_work(w, mode: str, pairs: float, ident: int = 0) -> dict:
     1 exponential per raster pair).  mode 'autograd' runs a forward-only pass (raster, rows,
     columns, loss rows without gradient) before the fused step.  `ident` planes propagate by
     the identity and need no transform: the column and loss-row passes count only the other
-    Lp = L - ident planes, and the identity planes' pixel-domain loss pass is added."""
+    Lp = L - ident planes, and the forward raster takes their loss (every launch reads their
+    targets, the launch with the gradient writes the seed)."""
     import math
     H, W, C, L = w.H, w.W, w.C, w.L
     Lp = L - ident
@@ -114,14 +114,12 @@ def step_work(w, mode: str, pairs: float, ident: int = 0) -> dict:
         else:
             work["k_rows_loss"] = grad_rows + (1,)
     if ident:
-        # reads U(0) and the identity planes' targets; the launch with the gradient also
+        # the identity planes' loss in the forward raster's epilogue: every launch reads their
+        # targets (6 flops per pixel, plane and channel); the launch with the gradient also
         # writes the seed
-        grad_id = ((2 + 0.5 * ident) * C * S, 6.0 * ident * C * H * W, 0.0)
-        if mode == "autograd":
-            nograd_id = ((1 + 0.5 * ident) * C * S, 4.0 * ident * C * H * W, 0.0)
-            work["k_ident_loss"] = tuple(a + b for a, b in zip(nograd_id, grad_id)) + (2,)
-        else:
-            work["k_ident_loss"] = grad_id + (1,)
+        b, f, u, n = work["k_raster_fwd"]
+        work["k_raster_fwd"] = (b + n * 0.5 * ident * C * S + C * S,
+                                f + n * 6.0 * ident * C * H * W, u, n)
     return work
 
 

@@ -119,7 +119,8 @@ cgh_status cgh_plan_set_workspace(cgh_plan* plan, void* workspace, size_t bytes)
  *                and skip the FFT passes; 2: propagate every plane through the FFT passes.
  *                Both compute the same loss and gradients (the first without the FFT
  *                round-off of an identity transform).  cgh_blasm_fwd/bwd always propagate
- *                every plane. */
+ *                every plane.  A plan that has such planes sizes its workspace for C x H x W
+ *                complex values more (their gradient seed, later dL/dU(0)). */
 typedef struct {
   int32_t col_block;
   int32_t row_block;

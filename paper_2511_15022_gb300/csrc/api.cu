@@ -93,9 +93,10 @@ static void layout(cgh_plan* p) {
   if (p->pair_capacity > 0x7fffffffLL) p->pair_capacity = 0x7fffffffLL;
   const size_t HW = (size_t)p->H * p->W;
   const size_t half = (size_t)p->H * p->bl.Nx;
-  // loss partials: one per CTA of the loss row pass (at most H L C), plus one per row and
-  // channel of the identity planes' pass
-  p->loss_slots = p->H * p->L * p->C + p->H * p->C + 1024;
+  // loss partials: one per CTA of the loss row pass (at most H L C), plus those of the
+  // identity planes' pass: one per tile (fused into the forward raster) or one per row and
+  // channel (the persistent batched step)
+  p->loss_slots = p->H * p->L * p->C + p->H * p->C + (int)T + 1024;
   size_t o = 0;
   p->off_rec = o;        o = align256(o + N * CGH_REC_F4 * sizeof(float4));
   p->off_rect = o;       o = align256(o + N * sizeof(int4));
@@ -108,6 +109,8 @@ static void layout(cgh_plan* p) {
   p->off_U0 = o;         o = align256(o + (size_t)p->C * HW * sizeof(float2));
   p->off_Y = o;          o = align256(o + (size_t)p->C * half * sizeof(float2));
   p->off_V = o;          o = align256(o + (size_t)p->L * p->C * half * sizeof(float2));
+  // the identity planes' gradient seed, later dL/dU(0) (plans with such planes only)
+  p->off_S = o;          o = align256(o + (p->n_ident > 0 ? (size_t)p->C * HW * sizeof(float2) : 0));
   p->ws_needed = o;
 }
 
@@ -508,8 +511,9 @@ extern "C" cgh_status cgh_intensity_bwd(cgh_plan* plan, const void* Ud, const fl
 }
 
 // Planes whose propagation is the identity are handled in the pixel domain when the plan
-// allows it: their loss and gradient seed come from U(0) directly (k_ident_loss), and only the
-// other planes go through the column and loss row passes.
+// allows it: their loss and gradient seed are taken on U(0) by the forward raster as it
+// finishes each pixel (the seed into the workspace's S), and only the other planes go
+// through the column and loss row passes.
 static bool ident_path(const cgh_plan* p) { return p->use_ident && p->n_ident > 0; }
 
 static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const float* target,
@@ -519,18 +523,24 @@ static cgh_status forward_chain(cgh_plan* plan, const cgh_params* params, const 
   float2* Y = (float2*)(plan->ws + plan->off_Y);
   float2* V = (float2*)(plan->ws + plan->off_V);
   float* partials = (float*)(plan->ws + plan->off_loss);
-  CGH_TRY(launch_raster_fwd(plan, params, U0, s, rebin), "raster_fwd");
   if (!ident_path(plan)) {
+    CGH_TRY(launch_raster_fwd(plan, params, U0, s, rebin), "raster_fwd");
     CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
     CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s), "cols_fwd_planes");
     CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad, loss_out), "rows_loss");
     return CGH_OK;
   }
   const BlasmDev* prop = &plan->bl_prop;
+  IdentLoss il;
+  il.target = target;
+  il.partials = partials + rows_loss_blocks(plan, prop);  // after the loss row pass's own
+  il.seed = want_grad ? (float2*)(plan->ws + plan->off_S) : nullptr;
+  il.recon_mask = plan->bl.recon_mask;
+  il.gscale = 4.0f / ((float)plan->L * (float)plan->C * (float)plan->H * (float)plan->W);
+  il.mask = plan->ident_mask;
+  il.loss_kind = plan->bl.loss_kind;
+  CGH_TRY(launch_raster_fwd(plan, params, U0, s, rebin, &il), "raster_fwd");
   if (prop->L > 0) CGH_TRY(launch_rows_pad_fwd(plan, U0, Y, plan->C, s), "rows_pad_fwd");
-  // after the row pass has read U(0): the identity planes' seed replaces it in place
-  const int own = rows_loss_blocks(plan, prop);
-  CGH_TRY(launch_ident_loss(plan, U0, target, partials + own, want_grad, s), "ident_loss");
   CGH_TRY(launch_cols_fwd_planes(plan, Y, V, s, prop), "cols_fwd_planes");
   CGH_TRY(launch_rows_loss(plan, V, target, partials, s, want_grad, loss_out, prop,
                            ident_loss_blocks(plan)), "rows_loss");
@@ -551,19 +561,23 @@ static cgh_status step_impl(cgh_plan* plan, const cgh_params* params, const floa
   if (!params || !target || !loss_out) return fail(CGH_ERR_ARG, "NULL argument");
   CGH_CHECK(check_grads(params, grads));
   CGH_CHECK(forward_chain(plan, params, target, loss_out, true, s, rebin));
-  float2* U0 = (float2*)(plan->ws + plan->off_U0);  // reused for dL/dU(0)
   float2* Y = (float2*)(plan->ws + plan->off_Y);    // reused for the backward half grid
   float2* V = (float2*)(plan->ws + plan->off_V);
+  float2* dU0;  // dL/dU(0)
   if (!ident_path(plan)) {
+    dU0 = (float2*)(plan->ws + plan->off_U0);  // U(0) is no longer needed
     CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s), "cols_bwd_planes");
-    CGH_TRY(launch_rows_inv_crop(plan, Y, U0, plan->C, s), "rows_inv_crop");
-  } else if (plan->bl_prop.L > 0) {
-    // dL/dU(0) = identity planes' seed (already in U0) + adjoint of the propagated planes
-    CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s, &plan->bl_prop), "cols_bwd_planes");
-    CGH_TRY(launch_rows_inv_crop(plan, Y, U0, plan->C, s, true), "rows_inv_crop");
+    CGH_TRY(launch_rows_inv_crop(plan, Y, dU0, plan->C, s), "rows_inv_crop");
+  } else {
+    // identity planes' seed (in S) + adjoint of the propagated planes
+    dU0 = (float2*)(plan->ws + plan->off_S);
+    if (plan->bl_prop.L > 0) {
+      CGH_TRY(launch_cols_bwd_planes(plan, V, Y, s, &plan->bl_prop), "cols_bwd_planes");
+      CGH_TRY(launch_rows_inv_crop(plan, Y, dU0, plan->C, s, true), "rows_inv_crop");
+    }
   }
   // the forward's binning is still valid for these parameters: reuse it
-  CGH_TRY(launch_raster_bwd(plan, params, U0, grads, s, false, grad_scale), "raster_bwd");
+  CGH_TRY(launch_raster_bwd(plan, params, dU0, grads, s, false, grad_scale), "raster_bwd");
   return CGH_OK;
 }
 

@@ -99,7 +99,7 @@ int rows_loss_blocks(const cgh_plan* p, const BlasmDev* planes) {
   return ((p->H + p->row_block - 1) / p->row_block) * L * p->C;
 }
 
-int ident_loss_blocks(const cgh_plan* p) { return p->H * p->C; }  // one per row and channel
+int ident_loss_blocks(const cgh_plan* p) { return p->tiles_x * p->tiles_y; }  // one per tile
 
 int pointwise_loss_blocks(const cgh_plan* p) {
   (void)p;
@@ -216,16 +216,6 @@ cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float*
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_loss_finalize(p, partials, rows_loss_blocks(p, &bl) + extra, loss_out, s);
-}
-
-cudaError_t launch_ident_loss(cgh_plan* p, float2* U, const float* target, float* partials,
-                              bool want_grad, cudaStream_t s) {
-  const float gscale = 4.0f / ((float)p->L * (float)p->C * (float)p->H * (float)p->W);
-  prof_begin(KID_IDENT_LOSS, s);
-  k_ident_loss<<<dim3(p->H, p->C), 256, 0, s>>>(p->bl, p->ident_mask, gscale, U, target,
-                                                partials, want_grad ? 1 : 0);
-  prof_end(KID_IDENT_LOSS, s);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s,

@@ -276,7 +276,8 @@ __global__ void k_loss_pointwise(const __grid_constant__ BlasmDev bl, long long 
 
 // Loss and gradient seed of the planes whose propagation is the identity (distance 0, no
 // aperture, every bin inside the band: H = 1 in Algorithm 3, so U(d_l) = U(0)), taken on
-// U(0) itself.  One CTA per image row y (blockIdx.x) and channel c (blockIdx.y); per pixel,
+// U(0) itself, as one work item of the persistent batched step (the planned step takes it in
+// the forward raster's epilogue instead).  One CTA per image row y and channel c; per pixel,
 // for each such plane l, d = |U|^2 - T_l: the loss partial gains w_l d^2 and the seed
 // sum_l gscale w_l d U (the seed the loss row pass forms, Sec. 3.2) replaces U when
 // want_grad (each element read and written by one thread).  Each thread loads its kIdentU
@@ -331,18 +332,6 @@ __device__ __forceinline__ void ident_loss_item(const BlasmDev& bl, unsigned mas
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[partial_index] = tot;
 }
-
-#ifndef CGH_ITEMS_ONLY
-__global__ void __launch_bounds__(256) k_ident_loss(const __grid_constant__ BlasmDev bl,
-                                                    unsigned mask, float gscale,
-                                                    float2* __restrict__ U,
-                                                    const float* __restrict__ target,
-                                                    float* __restrict__ partials, int want_grad) {
-  __shared__ float red[32];
-  ident_loss_item(bl, mask, gscale, U, target, partials, blockIdx.y * gridDim.x + blockIdx.x,
-                  want_grad, blockIdx.x, blockIdx.y, red);
-}
-#endif  // CGH_ITEMS_ONLY
 
 // Intensity of a complex field (Sec. 3.2: I = |U|^2), element-wise over `total` values.
 #ifndef CGH_ITEMS_ONLY

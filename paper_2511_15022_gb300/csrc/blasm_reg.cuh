@@ -155,12 +155,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // tstage = 1: the CTA's NB target rows are copied into shared memory (after the exchange
 // buffer) with asynchronous 16-byte copies issued before the inverse transform, so their
 // latency hides behind it (needs a 16-byte aligned target and W % 4 == 0).
-template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+// GRAD = false: loss only (the forward-only pass), compiled without the forward transform
+// so that none of its register pressure reaches the loss-only kernel.
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool GRAD>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_constant__ BlasmDev bl,
                                                   const float2* __restrict__ tw,
                                                   float2* __restrict__ V,
                                                   const float* __restrict__ target,
-                                                  float* __restrict__ partials, int want_grad,
+                                                  float* __restrict__ partials,
                                                   int tstage, float* __restrict__ loss_out,
                                                   int* __restrict__ ticket, double inv_norm,
                                                   int extra) {
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   });
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
-  if (want_grad) {
+  if constexpr (GRAD) {
     reg::first_in_regs<N, F::A, NB, T, false>(u);
     float2 w[F::GC::MB][F::C];
     // block_sum's barriers follow the inverse transform's last reads of buf
@@ -445,14 +447,15 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
     }
     default: {
       const int tstage = (p->W % 4 == 0 && (reinterpret_cast<uintptr_t>(a->target) & 15u) == 0);
-      auto k = kr_rows_loss<N, R0, R1, R2, NB, CB, T>;
+      auto k = a->want_grad ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, true>
+                            : kr_rows_loss<N, R0, R1, R2, NB, CB, T, false>;
       constexpr bool db = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
       const size_t smem = P::SMEM + (db ? sizeof(float2) * (size_t)P::BUF2 : 0) +
                           (tstage ? sizeof(float) * (size_t)NB * p->W : 0);
       e = reg_set_smem(k, smem, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_LOSS, s);
-      k<<<grid, T, smem, s>>>(bl, tw, a->out, a->target, a->partials, a->want_grad, tstage,
+      k<<<grid, T, smem, s>>>(bl, tw, a->out, a->target, a->partials, tstage,
                               a->loss_out, a->ticket, a->inv_norm, a->extra);
       prof_end(KID_ROWS_LOSS, s);
       break;

@@ -105,7 +105,7 @@ struct cgh_plan {
   size_t ws_bytes;
   // workspace carve-up (byte offsets)
   size_t off_rec, off_rect, off_raw, off_tile_count, off_tile_start, off_tile_cursor,
-      off_pairs, off_status, off_loss, off_U0, off_Y, off_V, ws_needed;
+      off_pairs, off_status, off_loss, off_U0, off_Y, off_V, off_S, ws_needed;
   int64_t pair_capacity;
   int loss_slots;
   // parameters the binning in the workspace was built for (bin_valid = 0: none)
@@ -133,8 +133,21 @@ LaunchShape fft_shape(const cgh_plan* p, const FFTDesc& d, int nb, int buffers);
 // raster.cu
 // rebin = false reuses the binning in the workspace when it was built for these parameter
 // pointers and N (the caller vouches for the values); otherwise the Gaussians are binned.
+// The identity planes' loss taken in the forward raster's epilogue: for every pixel of U(0),
+// channel c and plane l in `mask`, w (|U|^2 - T_l)^2 (w of loss_weight) summed into one
+// partial per tile, partials[ty * tiles_x + tx]; with `seed` non-NULL also
+// seed = gscale sum_l w (|U|^2 - T_l) U, in the layout of U (C x H x W).
+struct IdentLoss {
+  const float* target;              // [Ltot][C][H][W]
+  float* partials;                  // tiles_x * tiles_y
+  float2* seed;                     // NULL: the loss only
+  const unsigned char* recon_mask;  // L_recon depth masks [Ltot][H][W] (NULL: M = 0)
+  float gscale;                     // 4 / (Ltot C H W)
+  unsigned mask;                    // bit l: hologram plane l
+  int loss_kind;                    // 0: intensity MSE; 1: three-term L_recon
+};
 cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s,
-                              bool rebin = true);
+                              bool rebin = true, const IdentLoss* ident = nullptr);
 // rebin = false reuses the binning left in the workspace by the preceding raster_fwd with
 // the same parameters.
 // grad_scale: device float multiplying every gradient (NULL: 1).
@@ -159,11 +172,7 @@ cudaError_t launch_rows_loss(cgh_plan* p, float2* V, const float* target, float*
                              const BlasmDev* planes = nullptr, int extra = 0);
 cudaError_t launch_cols_bwd_planes(cgh_plan* p, const float2* G, float2* D, cudaStream_t s,
                                    const BlasmDev* planes = nullptr);
-// Loss and gradient seed of the identity planes (ident_mask) on U(0), pixel domain: the loss
-// partials go to partials[0, ident_loss_blocks()); with want_grad the seed
-// sum_l 4 w_l (|U|^2 - T_l) U / (Ltot C H W) overwrites U.
-cudaError_t launch_ident_loss(cgh_plan* p, float2* U, const float* target, float* partials,
-                              bool want_grad, cudaStream_t s);
+// loss partials of the identity planes' pass (one per tile of the forward raster)
 int ident_loss_blocks(const cgh_plan* p);
 cudaError_t launch_loss_pointwise(cgh_plan* p, const float2* Ud, const float* target,
                                   float* partials, float2* dUd, cudaStream_t s);
@@ -215,7 +224,7 @@ enum KernelId {
   KID_PREPROCESS = 0, KID_SCAN_TILES, KID_EMIT, KID_RASTER_FWD, KID_RASTER_BWD,
   KID_GRAD_FINALIZE, KID_ROWS_PAD_FWD, KID_COLS_FWD_PLANES, KID_ROWS_LOSS,
   KID_COLS_BWD_PLANES, KID_ROWS_INV_CROP, KID_LOSS_POINTWISE, KID_LOSS_FINALIZE, KID_ADAM,
-  KID_ENCODER, KID_POH, KID_IDENT_LOSS, KID_PERSIST, KID_COUNT
+  KID_ENCODER, KID_POH, KID_PERSIST, KID_COUNT
 };
 // Bracket one kernel launch: records a CUDA event before and after it on its stream when
 // profiling is enabled; otherwise only the launch counter moves.

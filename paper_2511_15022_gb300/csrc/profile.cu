@@ -20,7 +20,7 @@ const char* kNames[KID_COUNT] = {
     "k_preprocess", "k_scan_tiles", "k_emit", "k_raster_fwd", "k_raster_bwd",
     "k_grad_finalize", "k_rows_pad_fwd", "k_cols_fwd_planes", "k_rows_loss",
     "k_cols_bwd_planes", "k_rows_inv_crop", "k_loss_pointwise", "k_loss_finalize", "k_adam",
-    "k_encoder", "k_poh", "k_ident_loss", "k_batch_persistent"};
+    "k_encoder", "k_poh", "k_batch_persistent"};
 }  // namespace
 
 void prof_begin(int kid, cudaStream_t s) {

@@ -14,11 +14,15 @@
 //   4. k_raster_fwd   one CTA per tile, one thread per pixel; the tile's Gaussians are
 //                     staged in shared memory 256 at a time; each warp owns an 8x4 pixel
 //                     block and visits only the staged Gaussians whose box touches it
-//                     (per-warp lists compacted with ballots).
-//   5. k_raster_bwd   one CTA per tile with the tile's dL/dU in shared memory; each warp
-//                     takes one Gaussian at a time and sweeps its box inside the tile,
-//                     accumulating the gradient moments in registers, then reduces them
-//                     across the warp with shuffles and adds them with global atomics.
+//                     (per-warp lists compacted with ballots).  In the fused step it also
+//                     takes the loss (and seed) of the planes at distance 0 on the finished
+//                     pixels.
+//   5. k_raster_bwd_region  one CTA per 32x32 region (2x2 tiles) with the region's dL/dU
+//                     in shared memory; every Gaussian is kept once per region (from the
+//                     first of its tiles inside it); warps draw the kept Gaussians from a
+//                     shared counter and sweep each one's box inside the region,
+//                     accumulating the gradient moments in registers, then reduce them
+//                     across the warp with shuffles and add them with global atomics.
 //   6. k_grad_finalize one thread per Gaussian: chain rule from the accumulated moments to
 //                     the pre-activation parameters (Suppl. items 1-7; the
 //                     inverse-covariance -> covariance step is the exact derivative of the
@@ -103,8 +107,18 @@ static bool same_params(const cgh_params* a, const cgh_params* b) {
          a->alpha_raw == b->alpha_raw;
 }
 
+template <int C>
+static void raster_fwd_c(dim3 grid, cudaStream_t s, const RasterConsts& rc, const float4* rec,
+                         const int4* rect, const int* ts, const int* pairs, float2* U,
+                         const IdentLoss* ident) {
+  if (ident)
+    k_raster_fwd<C, true><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U, *ident);
+  else
+    k_raster_fwd<C, false><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U, IdentLoss{});
+}
+
 cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cudaStream_t s,
-                              bool rebin) {
+                              bool rebin, const IdentLoss* ident) {
   const bool reuse = !rebin && p->bin_valid && same_params(&p->bin_params, prm);
   cudaError_t e = reuse ? cudaSuccess : bin(p, prm, s);
   if (e != cudaSuccess) return e;
@@ -116,10 +130,10 @@ cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cud
   const int* pairs = (const int*)(p->ws + p->off_pairs);
   prof_begin(KID_RASTER_FWD, s);
   switch (p->C) {
-    case 1: k_raster_fwd<1><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
-    case 2: k_raster_fwd<2><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
-    case 3: k_raster_fwd<3><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
-    default: k_raster_fwd<4><<<grid, 256, 0, s>>>(rc, rec, rect, ts, pairs, U); break;
+    case 1: raster_fwd_c<1>(grid, s, rc, rec, rect, ts, pairs, U, ident); break;
+    case 2: raster_fwd_c<2>(grid, s, rc, rec, rect, ts, pairs, U, ident); break;
+    case 3: raster_fwd_c<3>(grid, s, rc, rec, rect, ts, pairs, U, ident); break;
+    default: raster_fwd_c<4>(grid, s, rc, rec, rect, ts, pairs, U, ident); break;
   }
   prof_end(KID_RASTER_FWD, s);
   return cudaGetLastError();

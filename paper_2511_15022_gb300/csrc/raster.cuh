@@ -17,7 +17,8 @@
 #ifndef CGH_WS_LOAD
 #define CGH_WS_LOAD(p) __ldg(p)
 #endif
-// ... and of data a kernel reads and later rewrites itself (the tile counters of the scan)
+// ... and of data a kernel reads that its own later phases rewrite (the tile counters the scan
+// reads and the emit counts down)
 #ifndef CGH_RW_LOAD
 #define CGH_RW_LOAD(p) (*(p))
 #endif
@@ -27,6 +28,25 @@ namespace cgh {
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kP2Floor = -50.0f * 1.4426950408889634f;  // power clamp -50 in log2 units
 constexpr float kAlphaCap = 0.99f;
+
+// 2^max(x, kP2Floor) with the hardware base-2 exponential (PTX ex2.approx.ftz.f32).  The
+// argument is clamped at kP2Floor (about -72), so every result is a normal number and the
+// flush-to-zero mode never applies; the instruction's relative error (about 2^-22) is far
+// inside the field and gradient tolerances.
+__device__ __forceinline__ float pow2_clamped(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(fmaxf(x, kP2Floor)));
+  return y;
+}
+
+// Exponent of one Gaussian (log2 units) at offset (dx, dy) from its mean from the record's
+// first two float4s: r0.z dx^2 + r0.w dx dy + r1.x dy^2 (the record holds -log2(e) / 2 times
+// the inverse covariance, the cross term doubled).  One form for the forward and both
+// backward sweeps, so that they take the same cutoff decisions.
+__device__ __forceinline__ float gauss_power(const float4& r0, const float4& r1, float dx,
+                                             float dy) {
+  return fmaf(dx, fmaf(r0.z, dx, r0.w * dy), r1.x * dy * dy);
+}
 
 struct RasterConsts {
   int H, W, C, N, tiles_x, tiles_y;
@@ -163,7 +183,7 @@ __global__ void k_preprocess(RasterConsts rc, cgh_params p, float4* __restrict__
 #endif  // CGH_ITEMS_ONLY
 
 // Exclusive scan of tile counts (one CTA of 1024 threads).  tile_start has T+1 entries;
-// tile_count is reset to zero so that k_emit can use it as the per-tile cursor.
+// tile_count is left as it is: k_emit counts it down to zero as the per-tile cursor.
 // The tiles are scanned in chunks of at most kScanChunk, each staged through shared memory
 // so that global memory is read and written with coalesced accesses (with one CTA doing the
 // whole scan, per-thread chunks read straight from global memory would cost one L1 wavefront
@@ -186,8 +206,21 @@ __device__ __forceinline__ void scan_tiles_cta(int T, long long cap, int* __rest
   for (int c0 = 0; c0 < T; c0 += chunk) {
     const int n = min(chunk, T - c0);
     __syncthreads();  // the previous chunk's stage has been written out
-    for (int i = tid; i < n; i += nt)
-      stage[scan_pad(i)] = CGH_RW_LOAD(&tile_count[(size_t)(c0 + i) * CGH_COUNT_STRIDE]);
+    // kScanU independent loads in flight per thread before any of them is stored
+    constexpr int kScanU = 8;
+    for (int i0 = tid; i0 < n; i0 += nt * kScanU) {
+      int cv[kScanU];
+#pragma unroll
+      for (int u = 0; u < kScanU; ++u) {
+        const int i = i0 + u * nt;
+        cv[u] = i < n ? CGH_RW_LOAD(&tile_count[(size_t)(c0 + i) * CGH_COUNT_STRIDE]) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kScanU; ++u) {
+        const int i = i0 + u * nt;
+        if (i < n) stage[scan_pad(i)] = cv[u];
+      }
+    }
     __syncthreads();
     const int per = (n + nt - 1) / nt;
     const int beg = min(n, tid * per), end = min(n, beg + per);
@@ -219,10 +252,7 @@ __device__ __forceinline__ void scan_tiles_cta(int T, long long cap, int* __rest
     }
     carry += warp_sums[(nt >> 5) - 1];
     __syncthreads();
-    for (int i = tid; i < n; i += nt) {
-      tile_start[c0 + i] = stage[scan_pad(i)];
-      tile_count[(size_t)(c0 + i) * CGH_COUNT_STRIDE] = 0;  // k_emit's per-tile cursor
-    }
+    for (int i = tid; i < n; i += nt) tile_start[c0 + i] = stage[scan_pad(i)];
   }
   if (tid == 0) {
     tile_start[T] = (int)min(carry, (long long)0x7fffffff);
@@ -246,7 +276,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int T, long long cap,
 // The (Gaussian, tile) slots.  A warp pools the boxes of its 32 Gaussians and deals the
 // (Gaussian, tile) items out to its lanes, EMIT_U per lane per round, so that one large box
 // (optimised Gaussians can grow to cover a hundred tiles) costs its warp a few rounds instead
-// of a long serial loop in one lane; each round's cursor increments are all in flight at once.
+// of a long serial loop in one lane; each round's cursor updates are all in flight at once.
 constexpr int EMIT_U = 4;
 // Called by all 32 lanes of a warp together, Gaussian n per lane (n >= N: no box).
 __device__ __forceinline__ void emit_warp(const RasterConsts& rc, const int4* __restrict__ rect,
@@ -285,7 +315,8 @@ __device__ __forceinline__ void emit_warp(const RasterConsts& rc, const int4* __
       const int ox = __shfl_sync(0xffffffffu, r.x, o), oy = __shfl_sync(0xffffffffu, r.y, o);
       gid[u] = warp_n0 + o;
       t[u] = k < total ? (oy + j / obw) * rc.tiles_x + ox + j % obw : -1;
-      slot[u] = t[u] >= 0 ? atomicAdd(&cursor[t[u] * CGH_COUNT_STRIDE], 1) : 0;
+      // the tile's count, counted down: slots count-1, ..., 0 (it ends at zero)
+      slot[u] = t[u] >= 0 ? atomicSub(&cursor[t[u] * CGH_COUNT_STRIDE], 1) - 1 : 0;
     }
 #pragma unroll
     for (int u = 0; u < EMIT_U; ++u) {
@@ -333,8 +364,9 @@ __device__ __forceinline__ int stage_batch(const RasterConsts& rc, const float4*
 // Gaussian also marks which warp blocks its box touches; each warp then compacts its own
 // list with ballots and visits only those Gaussians.
 // One tile (tx, ty) by a CTA of 256 threads; shared memory: srec[256 * CGH_REC_F4],
-// smask[256], slist[8][256].
-template <int C>
+// smask[256], slist[8][256] (+ red[8] with LOSS).  LOSS: the identity planes' loss (and
+// seed) of IdentLoss on the finished pixels, whose values are still in registers.
+template <int C, bool LOSS = false>
 __device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
                                                 const float4* __restrict__ rec,
                                                 const int4* __restrict__ rect,
@@ -342,7 +374,9 @@ __device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
                                                 const int* __restrict__ pairs,
                                                 float2* __restrict__ U, int tx, int ty,
                                                 float4* srec, unsigned char* smask,
-                                                unsigned char (*slist)[256]) {
+                                                unsigned char (*slist)[256],
+                                                const IdentLoss* il = nullptr,
+                                                float* red = nullptr) {
   const int tile = ty * rc.tiles_x + tx;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wx0 = tx * CGH_TILE + (warp & 1) * 8, wy0 = ty * CGH_TILE + (warp >> 1) * 4;
@@ -380,46 +414,99 @@ __device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
       cnt += __popc(b);
     }
     __syncwarp();
-    for (int t = 0; t < cnt; ++t) {
-      const int j = slist[warp][t];
-      const float4 r0 = srec[j * CGH_REC_F4 + 0];
-      const float4 r1 = srec[j * CGH_REC_F4 + 1];
-      const float dx = fpx - r0.x, dy = fpy - r0.y;
-      const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
-      if (p2 >= r1.y) {
-        const float G = exp2f(fmaxf(p2, kP2Floor));
-        const float a = fminf(kAlphaCap, r1.z * G);
-        const float4 r3 = srec[j * CGH_REC_F4 + 3];
-        const float4 r4 = srec[j * CGH_REC_F4 + 4];
-        const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
-        const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+    // contribution of the Gaussian whose record starts at srec[j] (power p2 >= its cutoff)
+    auto splat = [&](int j, float p2, float alpha) {
+      const float a = fminf(kAlphaCap, alpha * pow2_clamped(p2));
+      const float4 r3 = srec[j + 3];
+      const float4 r4 = srec[j + 4];
+      const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+      const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          accr[c] = fmaf(a, Ac[c], accr[c]);
-          acci[c] = fmaf(a, Bc[c], acci[c]);
+      for (int c = 0; c < C; ++c) {
+        accr[c] = fmaf(a, Ac[c], accr[c]);
+        acci[c] = fmaf(a, Bc[c], acci[c]);
+      }
+    };
+    // the warp's Gaussians two at a time, in list order: both records' geometry is read
+    // before either power is tested (more loads in flight, half the loop overhead)
+    int t = 0;
+    for (; t + 2 <= cnt; t += 2) {
+      const int j0 = slist[warp][t] * CGH_REC_F4, j1 = slist[warp][t + 1] * CGH_REC_F4;
+      const float4 a0 = srec[j0], b0 = srec[j0 + 1];
+      const float4 a1 = srec[j1], b1 = srec[j1 + 1];
+      const float p0 = gauss_power(a0, b0, fpx - a0.x, fpy - a0.y);
+      const float p1 = gauss_power(a1, b1, fpx - a1.x, fpy - a1.y);
+      if (p0 >= b0.y) splat(j0, p0, b0.z);
+      if (p1 >= b1.y) splat(j1, p1, b1.z);
+    }
+    if (t < cnt) {
+      const int j0 = slist[warp][t] * CGH_REC_F4;
+      const float4 a0 = srec[j0], b0 = srec[j0 + 1];
+      const float p0 = gauss_power(a0, b0, fpx - a0.x, fpy - a0.y);
+      if (p0 >= b0.y) splat(j0, p0, b0.z);
+    }
+  }
+  const bool inside = px < rc.W && py < rc.H;
+  const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
+  if (inside) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) U[c * plane + o] = make_float2(accr[c], acci[c]);
+  }
+  if constexpr (LOSS) {
+    // identity planes (U(d_l) = U(0)): per plane l and channel c, d = |U|^2 - T_l and the
+    // weight w of the loss (1, or 1 + M + T^2 for L_recon, Sec. 3.2); the tile's sum of
+    // w d^2 is one loss partial, the seed gscale sum_l w d U the loss row pass would form
+    float acc = 0.f;
+    if (inside) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const float I = fmaf(accr[c], accr[c], acci[c] * acci[c]);
+        float gs = 0.f;
+        for (unsigned m = il->mask; m != 0u; m &= m - 1u) {
+          const int l = __ffs((int)m) - 1;
+          const float t = __ldg(&il->target[((size_t)l * C + c) * plane + o]);
+          const float d = I - t;
+          float w = 1.f;
+          if (il->loss_kind != 0) {
+            const float mk =
+                (il->recon_mask && il->recon_mask[((size_t)l * rc.H + py) * rc.W + px]) ? 1.f : 0.f;
+            w = 1.f + mk + t * t;
+          }
+          const float wd = w * d;
+          acc = fmaf(wd, d, acc);
+          gs += wd;
+        }
+        if (il->seed) {
+          const float g = il->gscale * gs;
+          il->seed[c * plane + o] = make_float2(accr[c] * g, acci[c] * g);
         }
       }
     }
-  }
-  if (px < rc.W && py < rc.H) {
-    const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
-#pragma unroll
-    for (int c = 0; c < C; ++c) U[c * plane + o] = make_float2(accr[c], acci[c]);
+    for (int k = 16; k > 0; k >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, k);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tot = 0.f;
+      for (int w = 0; w < 8; ++w) tot += red[w];
+      il->partials[tile] = tot;
+    }
   }
 }
 
 #ifndef CGH_ITEMS_ONLY
-template <int C>
+// LOSS: with the identity planes' loss of `il` (one partial per tile).
+template <int C, bool LOSS>
 __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float4* __restrict__ rec,
                                                     const int4* __restrict__ rect,
                                                     const int* __restrict__ tile_start,
                                                     const int* __restrict__ pairs,
-                                                    float2* __restrict__ U) {
+                                                    float2* __restrict__ U, IdentLoss il) {
   __shared__ float4 srec[256 * CGH_REC_F4];
   __shared__ unsigned char smask[256];
   __shared__ unsigned char slist[8][256];
-  raster_fwd_tile<C>(rc, rec, rect, tile_start, pairs, U, blockIdx.x, blockIdx.y, srec, smask,
-                     slist);
+  __shared__ float red[8];
+  raster_fwd_tile<C, LOSS>(rc, rec, rect, tile_start, pairs, U, blockIdx.x, blockIdx.y, srec,
+                           smask, slist, &il, red);
 }
 #endif  // CGH_ITEMS_ONLY
 
@@ -521,10 +608,10 @@ __device__ __forceinline__ void raster_bwd_tile(const RasterConsts& rc,
         const int lx_ = x0 + (k - ry * bw), ly_ = y0 + ry;
         {
           const float dx = (float)(ox + lx_) - r0.x, dy = (float)(oy + ly_) - r0.y;
-          const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
+          const float p2 = gauss_power(r0, r1, dx, dy);
           if (p2 < r1.y) continue;
           const int pix = ly_ * CGH_TILE + lx_;
-          const float G = exp2f(fmaxf(p2, kP2Floor));
+          const float G = pow2_clamped(p2);
           const float aG = r1.z * G;
           const float a = fminf(kAlphaCap, aG);
           float S = 0.f;
@@ -580,8 +667,22 @@ __global__ void __launch_bounds__(256) k_raster_bwd(RasterConsts rc, const float
 // sweeps one kept Gaussian's box inside the region (up to 1024 pixels, flattened), with the
 // moments, reduction and atomics of raster_bwd_tile.  Compared with one CTA per tile, a
 // Gaussian that straddles tile borders is reduced once per region instead of once per tile.
-// Shared memory: srec[256 * CGH_REC_F4], sgid[256], sdu[C][1024], one int.
+// The four lists are walked as one stream of candidates (list q after lists 0..q-1), 256 per
+// batch; within a batch the warps take the kept Gaussians one at a time from a shared counter,
+// so a warp that drew small boxes takes more of them instead of waiting at the next barrier.
+// Shared memory: srec[256 * CGH_REC_F4], sgid[256], sdu[C][1024], then 16 ints: kept count,
+// next kept index, and per tile q of the region its list start [2 + q], candidate count
+// [6 + q] and exhaustive flag [10 + q].
 constexpr int kSuper = 2 * CGH_TILE;
+constexpr int kRegionCtl = 16;
+// 1 / w for box widths w = 1..32 (warp-uniform: one broadcast load instead of a division)
+static __constant__ float kInvWidth[kSuper + 1] = {
+    0.f,          1.f,          1.f / 2.f,    1.f / 3.f,    1.f / 4.f,    1.f / 5.f,
+    1.f / 6.f,    1.f / 7.f,    1.f / 8.f,    1.f / 9.f,    1.f / 10.f,   1.f / 11.f,
+    1.f / 12.f,   1.f / 13.f,   1.f / 14.f,   1.f / 15.f,   1.f / 16.f,   1.f / 17.f,
+    1.f / 18.f,   1.f / 19.f,   1.f / 20.f,   1.f / 21.f,   1.f / 22.f,   1.f / 23.f,
+    1.f / 24.f,   1.f / 25.f,   1.f / 26.f,   1.f / 27.f,   1.f / 28.f,   1.f / 29.f,
+    1.f / 30.f,   1.f / 31.f,   1.f / 32.f};
 template <int C>
 __device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
                                                   const float4* __restrict__ rec,
@@ -591,11 +692,26 @@ __device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
                                                   const float2* __restrict__ dU,
                                                   float* __restrict__ raw, int STX, int STY,
                                                   float4* srec, int* sgid,
-                                                  float2 (*sdu)[kSuper * kSuper], int* scount) {
+                                                  float2 (*sdu)[kSuper * kSuper], int* sctl) {
   constexpr int NV = 2 * C + 6;
   constexpr int NVP = NV <= 8 ? 8 : 16;  // padded to a power of two for the reduce-scatter
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int ox = STX * kSuper, oy = STY * kSuper;
+  if (threadIdx.x < 4) {
+    const int q = threadIdx.x;
+    const int sx = 2 * STX + (q & 1), sy = 2 * STY + (q >> 1);
+    int st = 0, cnt = 0, ex = 0;
+    if (sx < rc.tiles_x && sy < rc.tiles_y) {
+      const int tile = sy * rc.tiles_x + sx;
+      st = CGH_WS_LOAD(&tile_start[tile]);
+      const int end = CGH_WS_LOAD(&tile_start[tile + 1]);
+      ex = (long long)end > rc.cap;
+      cnt = ex ? rc.N : end - st;
+    }
+    sctl[2 + q] = st;
+    sctl[6 + q] = cnt;
+    sctl[10 + q] = ex;
+  }
   {
     const size_t plane = (size_t)rc.H * rc.W;
     for (int i = threadIdx.x; i < kSuper * kSuper; i += blockDim.x) {
@@ -607,70 +723,79 @@ __device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
         sdu[c][i] = inside ? CGH_WS_LOAD(&dU[c * plane + o]) : make_float2(0.f, 0.f);
     }
   }
+  __syncthreads();  // tile lists and dU are staged
+  const int e1 = sctl[6], e2 = e1 + sctl[7], e3 = e2 + sctl[8], total = e3 + sctl[9];
   const float fox = (float)ox, foy = (float)oy;
-  for (int q = 0; q < 4; ++q) {
-    const int sx = 2 * STX + (q & 1), sy = 2 * STY + (q >> 1);
-    if (sx >= rc.tiles_x || sy >= rc.tiles_y) continue;  // CTA-uniform
-    const int tile = sy * rc.tiles_x + sx;
-    const int start = CGH_WS_LOAD(&tile_start[tile]), end = CGH_WS_LOAD(&tile_start[tile + 1]);
-    const bool exhaustive = (long long)end > rc.cap;
-    const int count = exhaustive ? rc.N : end - start;
-    for (int base = 0; base < count; base += 256) {
-      __syncthreads();  // the previous batch has been swept; dU is staged
-      if (threadIdx.x == 0) *scount = 0;
-      __syncthreads();
-      const int i = base + threadIdx.x;
-      int gid = 0;
-      bool keep = false;
-      if (i < count) {
-        gid = exhaustive ? i : CGH_WS_LOAD(&pairs[start + i]);
-        const int4 r = CGH_WS_LOAD(&rect[gid]);
-        keep = r.x <= sx && sx <= r.z && r.y <= sy && sy <= r.w &&
-               sx == max(r.x, 2 * STX) && sy == max(r.y, 2 * STY);
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      int wbase = 0;
-      if (lane == 0 && bal) wbase = atomicAdd(scount, __popc(bal));
-      wbase = __shfl_sync(0xffffffffu, wbase, 0);
-      if (keep) {
-        const int slot = wbase + __popc(bal & ((1u << lane) - 1u));
-        const float4* g = rec + (size_t)gid * CGH_REC_F4;
+  for (int base = 0; base < total; base += 256) {
+    __syncthreads();  // the previous batch has been swept
+    if (threadIdx.x == 0) { sctl[0] = 0; sctl[1] = 0; }
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    int gid = 0;
+    bool keep = false;
+    if (i < total) {
+      const int q = (i >= e1) + (i >= e2) + (i >= e3);
+      const int li = i - (q == 0 ? 0 : q == 1 ? e1 : q == 2 ? e2 : e3);
+      const int sx = 2 * STX + (q & 1), sy = 2 * STY + (q >> 1);
+      gid = sctl[10 + q] ? li : CGH_WS_LOAD(&pairs[sctl[2 + q] + li]);
+      const int4 r = CGH_WS_LOAD(&rect[gid]);
+      keep = r.x <= sx && sx <= r.z && r.y <= sy && sy <= r.w &&
+             sx == max(r.x, 2 * STX) && sy == max(r.y, 2 * STY);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    int wbase = 0;
+    if (lane == 0 && bal) wbase = atomicAdd(&sctl[0], __popc(bal));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    if (keep) {
+      const int slot = wbase + __popc(bal & ((1u << lane) - 1u));
+      const float4* g = rec + (size_t)gid * CGH_REC_F4;
 #pragma unroll
-        for (int k = 0; k < CGH_REC_F4; ++k) srec[slot * CGH_REC_F4 + k] = CGH_WS_LOAD(&g[k]);
-        sgid[slot] = gid;
-      }
-      __syncthreads();
-      const int nb = *scount;
-      for (int j = warp; j < nb; j += 8) {
-        const float4 bb = srec[j * CGH_REC_F4 + 2];
-        // pixel box of the Gaussian inside this region (region coordinates)
-        const int x0 = (int)ceilf(fmaxf(bb.x, fox)) - ox;
-        const int x1 = (int)floorf(fminf(bb.y, fox + (float)(kSuper - 1))) - ox;
-        const int y0 = (int)ceilf(fmaxf(bb.z, foy)) - oy;
-        const int y1 = (int)floorf(fminf(bb.w, foy + (float)(kSuper - 1))) - oy;
-        if (x0 > x1 || y0 > y1) continue;  // warp-uniform
-        const float4 r0 = srec[j * CGH_REC_F4 + 0];
-        const float4 r1 = srec[j * CGH_REC_F4 + 1];
-        const float4 r3 = srec[j * CGH_REC_F4 + 3];
-        const float4 r4 = srec[j * CGH_REC_F4 + 4];
-        const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
-        const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
-        // flattened box pixels: floor(k / bw) from one FP32 product, exact here because
-        // k < 1024 and the fractional part of (k + 1/2) / bw stays at least 1/64 away from an
-        // integer (relative rounding of the product below 2^-23 * 1024)
-        const int bw = x1 - x0 + 1, npx = bw * (y1 - y0 + 1);
-        const float inv_bw = 1.f / (float)bw;
-        float acc[NVP];
+      for (int k = 0; k < CGH_REC_F4; ++k) srec[slot * CGH_REC_F4 + k] = CGH_WS_LOAD(&g[k]);
+      sgid[slot] = gid;
+    }
+    __syncthreads();
+    const int nb = sctl[0];
+    for (;;) {
+      int j = 0;
+      if (lane == 0) j = atomicAdd(&sctl[1], 1);
+      j = __shfl_sync(0xffffffffu, j, 0);
+      if (j >= nb) break;  // warp-uniform
+      const float4 bb = srec[j * CGH_REC_F4 + 2];
+      // pixel box of the Gaussian inside this region (region coordinates)
+      const int x0 = (int)ceilf(fmaxf(bb.x, fox)) - ox;
+      const int x1 = (int)floorf(fminf(bb.y, fox + (float)(kSuper - 1))) - ox;
+      const int y0 = (int)ceilf(fmaxf(bb.z, foy)) - oy;
+      const int y1 = (int)floorf(fminf(bb.w, foy + (float)(kSuper - 1))) - oy;
+      if (x0 > x1 || y0 > y1) continue;  // warp-uniform
+      const float4 r0 = srec[j * CGH_REC_F4 + 0];
+      const float4 r1 = srec[j * CGH_REC_F4 + 1];
+      const float4 r3 = srec[j * CGH_REC_F4 + 3];
+      const float4 r4 = srec[j * CGH_REC_F4 + 4];
+      const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+      const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+      // the box's pixels, flattened: lane k takes pixels k, k + 32, ...  The lane's first
+      // pixel is found once (floor(k / bw) from one FP32 product, exact because k < 1024 and
+      // the fractional part of (k + 1/2) / bw stays at least 1/64 away from an integer), then
+      // each step moves q rows and r columns, one row more when the column passes the box.
+      // The pixel coordinates are carried as integer-valued floats (exact), so dx and dy are
+      // the same single roundings as in the forward pass.
+      const int bw = x1 - x0 + 1, npx = bw * (y1 - y0 + 1);
+      const float inv_bw = kInvWidth[bw];  // bw <= 32: the box lies inside the region
+      const int q = (int)(32.5f * inv_bw), r = 32 - q * bw;
+      const int ry0 = (int)(((float)lane + 0.5f) * inv_bw);
+      int lx = x0 + lane - ry0 * bw;
+      float fx = (float)(ox + lx), fy = (float)(oy + y0 + ry0);
+      int pix = (y0 + ry0) * kSuper + lx;
+      const float fr = (float)r, fq = (float)q, fbw = (float)bw;
+      const int xe = x0 + bw, dpix = q * kSuper + r;
+      float acc[NVP];
 #pragma unroll
-        for (int v = 0; v < NVP; ++v) acc[v] = 0.f;
-        for (int k = lane; k < npx; k += 32) {
-          const int ry = (int)(((float)k + 0.5f) * inv_bw);
-          const int lx_ = x0 + (k - ry * bw), ly_ = y0 + ry;
-          const float dx = (float)(ox + lx_) - r0.x, dy = (float)(oy + ly_) - r0.y;
-          const float p2 = fmaf(r0.z * dx, dx, fmaf(r0.w * dx, dy, r1.x * dy * dy));
-          if (p2 < r1.y) continue;
-          const int pix = ly_ * kSuper + lx_;
-          const float G = exp2f(fmaxf(p2, kP2Floor));
+      for (int v = 0; v < NVP; ++v) acc[v] = 0.f;
+      for (int k = lane; k < npx; k += 32) {
+        const float dx = fx - r0.x, dy = fy - r0.y;
+        const float p2 = gauss_power(r0, r1, dx, dy);
+        if (p2 >= r1.y) {
+          const float G = pow2_clamped(p2);
           const float aG = r1.z * G;
           const float a = fminf(kAlphaCap, aG);
           float S = 0.f;
@@ -694,11 +819,21 @@ __device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
             }
           }
         }
-        int vidx = 0;
-        ReduceScatter<NVP, 16>::run(acc, lane, vidx);
-        if ((lane & (32 / NVP - 1)) == 0 && vidx < NV && acc[0] != 0.f)
-          atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
+        lx += r;
+        fx += fr;
+        fy += fq;
+        pix += dpix;
+        if (lx >= xe) {
+          lx -= bw;
+          fx -= fbw;
+          fy += 1.f;
+          pix += kSuper - bw;
+        }
       }
+      int vidx = 0;
+      ReduceScatter<NVP, 16>::run(acc, lane, vidx);
+      if ((lane & (32 / NVP - 1)) == 0 && vidx < NV && acc[0] != 0.f)
+        atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
     }
   }
 }
@@ -716,16 +851,16 @@ __global__ void __launch_bounds__(256) k_raster_bwd_region(RasterConsts rc,
   float4* srec = reinterpret_cast<float4*>(smem_rb);
   int* sgid = reinterpret_cast<int*>(srec + 256 * CGH_REC_F4);
   float2(*sdu)[kSuper * kSuper] = reinterpret_cast<float2(*)[kSuper * kSuper]>(sgid + 256);
-  int* scount = reinterpret_cast<int*>(&sdu[C][0]);
+  int* sctl = reinterpret_cast<int*>(&sdu[C][0]);
   raster_bwd_region<C>(rc, rec, rect, tile_start, pairs, dU, raw, blockIdx.x, blockIdx.y, srec,
-                       sgid, sdu, scount);
+                       sgid, sdu, sctl);
 }
 #endif  // CGH_ITEMS_ONLY
 
 // shared memory of k_raster_bwd_region<C>
 __host__ __device__ constexpr size_t raster_bwd_region_smem(int C) {
   return sizeof(float4) * 256 * CGH_REC_F4 + sizeof(int) * 256 +
-         sizeof(float2) * (size_t)C * kSuper * kSuper + sizeof(int);
+         sizeof(float2) * (size_t)C * kSuper * kSuper + sizeof(int) * kRegionCtl;
 }
 
 template <int C>

@@ -54,8 +54,8 @@ def test_work_model_matches_the_fused_pass_count():
 
 def test_work_model_with_an_identity_plane():
     """With the plane at 0 mm taken in the pixel domain the column and loss-row passes count
-    the two propagated planes only, and the identity plane's loss pass reads U(0) and one
-    target plane and writes the seed, which the last row pass reads back."""
+    the two propagated planes only, and the forward raster reads one target plane and writes
+    the seed, which the last row pass reads back."""
     import bench
     from paper_2511_15022_gb300 import inputs
     w = inputs.hd_1080p()
@@ -65,7 +65,8 @@ def test_work_model_with_an_identity_plane():
     assert ident["k_cols_fwd_planes"][0] == (2 + 2 * 2) * w.C * S
     assert ident["k_cols_bwd_planes"][0] == (2 * 2 + 2) * w.C * S
     assert ident["k_rows_loss"][0] == 4.5 * 2 * w.C * S
-    assert ident["k_ident_loss"][0] == 2.5 * w.C * S
+    assert ident["k_raster_fwd"][0] == full["k_raster_fwd"][0] + 1.5 * w.C * S
+    assert "k_ident_loss" not in ident
     assert ident["k_rows_inv_crop"][0] == full["k_rows_inv_crop"][0] + w.C * S
     # one column transform of the four per column block fewer in each column pass
     assert abs(ident["k_cols_fwd_planes"][1] / full["k_cols_fwd_planes"][1] - 3 / 4) < 0.01
