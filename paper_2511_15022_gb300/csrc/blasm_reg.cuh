@@ -156,8 +156,10 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // buffer) with asynchronous 16-byte copies issued before the inverse transform, so their
 // latency hides behind it (needs a 16-byte aligned target and W % 4 == 0).
 // GRAD = false: loss only (the forward-only pass), compiled without the forward transform
-// so that none of its register pressure reaches the loss-only kernel.
-template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool GRAD>
+// so that none of its register pressure reaches the loss-only kernel.  GENERAL = false: the
+// intensity MSE (weight 1) with the target staged (tstage = 1), the common case, compiled
+// without the runtime choices, which keeps the gradient kernel inside its 64 registers.
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool GRAD, bool GENERAL>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_constant__ BlasmDev bl,
                                                   const float2* __restrict__ tw,
                                                   float2* __restrict__ V,
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   const float* tg = target + ((size_t)plane * bl.C + batch % bl.C) * H * W;
   float2* by = buf + P::BUF;  // second exchange buffer (DB)
   float* tsm = reinterpret_cast<float*>(buf + P::BUF + (DB ? P::BUF2 : 0));
+  if (!GENERAL) tstage = 1;
   if (tstage) {
     const int chunks = NB * (W / 4);
     for (int i = threadIdx.x; i < chunks; i += T) {
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
       const float I_ = fmaf(val.x, val.x, val.y * val.y);
       const float t_ = tstage ? tsm[b * W + x] : __ldg(&tg[(size_t)y * W + x]);
       const float d = I_ - t_;
-      const float wd = loss_weight(bl, plane, y, x, t_) * d;
+      const float wd = GENERAL ? loss_weight(bl, plane, y, x, t_) * d : d;
       acc = fmaf(wd, d, acc);
       val = cscale(val, gscale * wd);
     } else {
@@ -224,9 +227,11 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     // block_sum's barriers follow the inverse transform's last reads of buf
     if constexpr (DB) F::rest2(u, w, buf, by, tw);
     else F::template rest<false>(u, w, buf, tw);
+    // row and base re-derived from the block index (fewer values live across the transform)
+    float2* hv = V + (size_t)blockIdx.y * bl.H * N;
     reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
-      const int y = y0 + b;
-      if (y < H) half[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
+      const int y = blockIdx.x * NB + b;
+      if (y < bl.H) hv[((size_t)(a / CB) * bl.H + y) * CB + (a % CB)] = val;
     });
   }
   // at the end, where no transform state is live
@@ -447,8 +452,11 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
     }
     default: {
       const int tstage = (p->W % 4 == 0 && (reinterpret_cast<uintptr_t>(a->target) & 15u) == 0);
-      auto k = a->want_grad ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, true>
-                            : kr_rows_loss<N, R0, R1, R2, NB, CB, T, false>;
+      const bool general = !tstage || bl.loss_kind != 0;
+      auto k = a->want_grad ? (general ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, true, true>
+                                       : kr_rows_loss<N, R0, R1, R2, NB, CB, T, true, false>)
+                            : (general ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, false, true>
+                                       : kr_rows_loss<N, R0, R1, R2, NB, CB, T, false, false>);
       constexpr bool db = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
       const size_t smem = P::SMEM + (db ? sizeof(float2) * (size_t)P::BUF2 : 0) +
                           (tstage ? sizeof(float) * (size_t)NB * p->W : 0);

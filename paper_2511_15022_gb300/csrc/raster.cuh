@@ -773,61 +773,43 @@ __device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
       const float4 r4 = srec[j * CGH_REC_F4 + 4];
       const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
       const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
-      // the box's pixels, flattened: lane k takes pixels k, k + 32, ...  The lane's first
-      // pixel is found once (floor(k / bw) from one FP32 product, exact because k < 1024 and
-      // the fractional part of (k + 1/2) / bw stays at least 1/64 away from an integer), then
-      // each step moves q rows and r columns, one row more when the column passes the box.
-      // The pixel coordinates are carried as integer-valued floats (exact), so dx and dy are
-      // the same single roundings as in the forward pass.
+      // flattened box pixels: floor(k / bw) from one FP32 product with the correctly rounded
+      // 1 / bw (bw <= 32: the box lies inside the region), exact here because k < 1024 and
+      // the fractional part of (k + 1/2) / bw stays at least 1/64 away from an integer
       const int bw = x1 - x0 + 1, npx = bw * (y1 - y0 + 1);
-      const float inv_bw = kInvWidth[bw];  // bw <= 32: the box lies inside the region
-      const int q = (int)(32.5f * inv_bw), r = 32 - q * bw;
-      const int ry0 = (int)(((float)lane + 0.5f) * inv_bw);
-      int lx = x0 + lane - ry0 * bw;
-      float fx = (float)(ox + lx), fy = (float)(oy + y0 + ry0);
-      int pix = (y0 + ry0) * kSuper + lx;
-      const float fr = (float)r, fq = (float)q, fbw = (float)bw;
-      const int xe = x0 + bw, dpix = q * kSuper + r;
+      const float inv_bw = kInvWidth[bw];
       float acc[NVP];
 #pragma unroll
       for (int v = 0; v < NVP; ++v) acc[v] = 0.f;
       for (int k = lane; k < npx; k += 32) {
-        const float dx = fx - r0.x, dy = fy - r0.y;
+        const int ry = (int)(((float)k + 0.5f) * inv_bw);
+        const int lx_ = x0 + (k - ry * bw), ly_ = y0 + ry;
+        const float dx = (float)(ox + lx_) - r0.x, dy = (float)(oy + ly_) - r0.y;
         const float p2 = gauss_power(r0, r1, dx, dy);
-        if (p2 >= r1.y) {
-          const float G = pow2_clamped(p2);
-          const float aG = r1.z * G;
-          const float a = fminf(kAlphaCap, aG);
-          float S = 0.f;
+        if (p2 < r1.y) continue;
+        const int pix = ly_ * kSuper + lx_;
+        const float G = pow2_clamped(p2);
+        const float aG = r1.z * G;
+        const float a = fminf(kAlphaCap, aG);
+        float S = 0.f;
 #pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const float2 gv = sdu[c][pix];
-            acc[c] = fmaf(a, gv.x, acc[c]);
-            acc[C + c] = fmaf(a, gv.y, acc[C + c]);
-            S = fmaf(Ac[c], gv.x, fmaf(Bc[c], gv.y, S));
-          }
-          if (aG < kAlphaCap) {
-            acc[2 * C] = fmaf(S, G, acc[2 * C]);
-            if (p2 > kP2Floor) {
-              const float u = S * aG;
-              const float udx = u * dx, udy = u * dy;
-              acc[2 * C + 1] += udx;
-              acc[2 * C + 2] += udy;
-              acc[2 * C + 3] = fmaf(udx, dx, acc[2 * C + 3]);
-              acc[2 * C + 4] = fmaf(udx, dy, acc[2 * C + 4]);
-              acc[2 * C + 5] = fmaf(udy, dy, acc[2 * C + 5]);
-            }
-          }
+        for (int c = 0; c < C; ++c) {
+          const float2 gv = sdu[c][pix];
+          acc[c] = fmaf(a, gv.x, acc[c]);
+          acc[C + c] = fmaf(a, gv.y, acc[C + c]);
+          S = fmaf(Ac[c], gv.x, fmaf(Bc[c], gv.y, S));
         }
-        lx += r;
-        fx += fr;
-        fy += fq;
-        pix += dpix;
-        if (lx >= xe) {
-          lx -= bw;
-          fx -= fbw;
-          fy += 1.f;
-          pix += kSuper - bw;
+        if (aG < kAlphaCap) {
+          acc[2 * C] = fmaf(S, G, acc[2 * C]);
+          if (p2 > kP2Floor) {
+            const float u = S * aG;
+            const float udx = u * dx, udy = u * dy;
+            acc[2 * C + 1] += udx;
+            acc[2 * C + 2] += udy;
+            acc[2 * C + 3] = fmaf(udx, dx, acc[2 * C + 3]);
+            acc[2 * C + 4] = fmaf(udx, dy, acc[2 * C + 4]);
+            acc[2 * C + 5] = fmaf(udy, dy, acc[2 * C + 5]);
+          }
         }
       }
       int vidx = 0;
