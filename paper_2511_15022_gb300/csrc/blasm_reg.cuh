@@ -54,30 +54,63 @@ struct RegPlan {
 template <int N, int NB>
 constexpr size_t rows_stage_bytes() { return sizeof(float) * (size_t)NB * (N / 2); }
 
-template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+// Offset of element (row y, position a) of a column-blocked half grid (CB columns per
+// block): ((a / CB) H + y) CB + a % CB.  For the positions a = j + r M of one pass, with M a
+// multiple of CB, this is blk_base(j, y) + r M H: the butterfly's part is computed once and
+// each element adds one product (unsigned, so the division and remainder need no sign fix-up).
+template <int CB>
+__device__ __forceinline__ unsigned blk_base(int j, int y, int H) {
+  return ((unsigned)j / CB * (unsigned)H + (unsigned)y) * CB + (unsigned)j % CB;
+}
+
+// Image coordinate of position j + r M (0 <= j < M = N / R) of a pass over a padded length
+// N, and whether it lies inside the image window [off, off + len).  CA (centred window of half
+// the length: off = N / 4, len = N / 2, i.e. pad factor 2 with an even image size): the
+// coordinate is j plus a compile-time constant, and registers whose positions lie wholly
+// inside or wholly outside the window need no test at all (for R % 4 == 0 that is every
+// register); what their values feed is then folded or dropped at compile time.
+template <int N, int R, bool CA>
+__device__ __forceinline__ bool in_window(int j, int r, int off, int len, int& x) {
+  constexpr int M = N / R;
+  if constexpr (CA) {
+    x = j + (r * M - N / 4);
+    if (r * M + M <= N / 4 || r * M >= 3 * N / 4) return false;  // wholly outside
+    if (r * M >= N / 4 && r * M + M <= 3 * N / 4) return true;   // wholly inside
+    return (unsigned)x < (unsigned)(N / 2);
+  } else {
+    x = j - off + r * M;
+    return (unsigned)x < (unsigned)len;
+  }
+}
+
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool CA>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
                                                      const float2* __restrict__ tw,
                                                      const float2* __restrict__ in,
                                                      float2* __restrict__ half) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using F = typename P::F;
+  static_assert((N / F::C) % CB == 0, "column blocks must tile the output stride");
   constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), 0);
   extern __shared__ float2 buf[];
   const int batch = blockIdx.y, y0 = blockIdx.x * NB;
   const int H = bl.H, W = bl.W, ox = bl.ox;
   const float2* src = in + (size_t)batch * H * W;
   float2 v[F::GA::MB][F::A];
-  reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
-    const int x = a - ox, y = y0 + b;
-    return (x >= 0 && x < W && y < H) ? __ldg(&src[(size_t)y * W + x]) : make_float2(0.f, 0.f);
+  reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
+    const int y = y0 + b;
+    int x;
+    const bool in_img = in_window<N, F::A, CA>(j, r, ox, W, x);
+    return (in_img && y < H) ? __ldg(&src[(size_t)y * W + x]) : make_float2(0.f, 0.f);
   });
   float2 out[F::GC::MB][F::C];
   if constexpr (DB) F::rest2(v, out, buf, buf + P::BUF, tw);
   else F::template rest<false>(v, out, buf, tw);  // first transform: no earlier reader
   float2* dst = half + (size_t)batch * H * N;
-  reg::for_each<N, F::C, NB, T>(out, [&](int b, int a, float2& val) {
+  const unsigned MH = (unsigned)(N / F::C) * (unsigned)H;
+  reg::for_each_jr<N, F::C, NB, T>(out, [&](int b, int j, int r, float2& val) {
     const int y = y0 + b;
-    if (y < H) dst[((size_t)(a / CB) * H + y) * CB + (a % CB)] = val;
+    if (y < H) dst[blk_base<CB>(j, y, H) + (unsigned)r * MH] = val;
   });
 }
 
@@ -102,13 +135,14 @@ constexpr size_t rows_addend_bytes() { return sizeof(float2) * (size_t)NB * (N /
 // staged in shared memory (after the exchange buffers) by asynchronous 16-byte copies issued
 // before the transform, so their latency hides behind it (needs W even and a 16-byte
 // aligned `out`); accum = 2: out += them with plain loads in the epilogue.
-template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool ACC>
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool ACC, bool CA>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __grid_constant__ BlasmDev bl,
                                                       const float2* __restrict__ tw,
                                                       const float2* __restrict__ half,
                                                       float2* __restrict__ out, int accum) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   using I = typename P::I;
+  static_assert((N / I::A) % CB == 0, "column blocks must tile the input stride");
   constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), ACC ? rows_addend_bytes<N, NB>() : 0);
   if (!ACC) accum = 0;
   extern __shared__ float2 buf[];
@@ -118,17 +152,19 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
   float2* dst = out + (size_t)batch * H * W;
   float2* asm_ = buf + P::BUF + (DB ? P::BUF2 : 0);  // addend stage (accum = 1)
   if (accum == 1) {
-    const int chunks = NB * (W / 2);
-    for (int i = threadIdx.x; i < chunks; i += T) {
-      const int b = i / (W / 2), x = (i % (W / 2)) * 2;
-      if (y0 + b < H) cp_async16(&asm_[b * W + x], &dst[(size_t)(y0 + b) * W + x]);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (y0 + b >= H) break;
+      const float2* row = dst + (size_t)(y0 + b) * W;
+      for (int x = 2 * threadIdx.x; x < W; x += 2 * T) cp_async16(&asm_[b * W + x], &row[x]);
     }
     cp_async_commit();
   }
   float2 v[I::GA::MB][I::A];
-  reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
+  const unsigned MH = (unsigned)(N / I::A) * (unsigned)H;
+  reg::first_from_jr<N, I::A, NB, T, true>(v, [&](int b, int j, int r) {
     const int y = y0 + b;
-    return y < H ? __ldg(&src[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
+    return y < H ? __ldg(&src[blk_base<CB>(j, y, H) + (unsigned)r * MH]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
   if constexpr (DB) I::rest2(v, u, buf, buf + P::BUF, tw);
@@ -137,9 +173,10 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_inv_crop(const __g
     cp_async_wait_all();
     __syncthreads();
   }
-  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
-    const int x = a - ox, y = y0 + b;
-    if (x >= 0 && x < W && y < H) {
+  reg::for_each_jr<N, I::C, NB, T>(u, [&](int b, int j, int r, float2& val) {
+    const int y = y0 + b;
+    int x;
+    if (in_window<N, I::C, CA>(j, r, ox, W, x) && y < H) {
       float2* o = &dst[(size_t)y * W + x];
       if (accum == 1) val = cadd(asm_[b * W + x], val);
       else if (accum == 2) val = cadd(*o, val);  // each element read and written by one thread
@@ -159,7 +196,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // so that none of its register pressure reaches the loss-only kernel.  GENERAL = false: the
 // intensity MSE (weight 1) with the target staged (tstage = 1), the common case, compiled
 // without the runtime choices, which keeps the gradient kernel inside its 64 registers.
-template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool GRAD, bool GENERAL>
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool GRAD, bool GENERAL, bool CA>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_constant__ BlasmDev bl,
                                                   const float2* __restrict__ tw,
                                                   float2* __restrict__ V,
@@ -173,6 +210,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   using I = typename P::I;
   static_assert(I::C == F::A, "inverse must end where the forward starts");
   static_assert(T % 32 == 0, "the loss reduction shuffles over whole warps");
+  static_assert((N / I::A) % CB == 0 && (N / F::C) % CB == 0,
+                "column blocks must tile the input and output strides");
   constexpr bool DB = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
   extern __shared__ float2 buf[];
   __shared__ float red[32];
@@ -185,17 +224,19 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   float* tsm = reinterpret_cast<float*>(buf + P::BUF + (DB ? P::BUF2 : 0));
   if (!GENERAL) tstage = 1;
   if (tstage) {
-    const int chunks = NB * (W / 4);
-    for (int i = threadIdx.x; i < chunks; i += T) {
-      const int b = i / (W / 4), x = (i % (W / 4)) * 4;
-      if (y0 + b < H) cp_async16(&tsm[b * W + x], &tg[(size_t)(y0 + b) * W + x]);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (y0 + b >= H) break;
+      const float* row = tg + (size_t)(y0 + b) * W;
+      for (int x = 4 * threadIdx.x; x < W; x += 4 * T) cp_async16(&tsm[b * W + x], &row[x]);
     }
     cp_async_commit();
   }
   float2 v[I::GA::MB][I::A];
-  reg::first_from<N, I::A, NB, T, true>(v, [&](int b, int a) {
+  const unsigned MHI = (unsigned)(N / I::A) * (unsigned)H;
+  reg::first_from_jr<N, I::A, NB, T, true>(v, [&](int b, int j, int r) {
     const int y = y0 + b;
-    return y < H ? __ldg(&half[((size_t)(a / CB) * H + y) * CB + (a % CB)]) : make_float2(0.f, 0.f);
+    return y < H ? __ldg(&half[blk_base<CB>(j, y, H) + (unsigned)r * MHI]) : make_float2(0.f, 0.f);
   });
   float2 u[I::GC::MB][I::C];
   if constexpr (DB) I::rest2(v, u, buf, by, tw);
@@ -206,9 +247,10 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   }
   const float gscale = 4.0f / ((float)bl.Ltot * (float)bl.C * (float)H * (float)W);
   float acc = 0.f;
-  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float2& val) {
-    const int x = a - ox, y = y0 + b;
-    if (x >= 0 && x < W && y < H) {
+  reg::for_each_jr<N, I::C, NB, T>(u, [&](int b, int j, int r, float2& val) {
+    const int y = y0 + b;
+    int x;
+    if (in_window<N, I::C, CA>(j, r, ox, W, x) && y < H) {
       const float I_ = fmaf(val.x, val.x, val.y * val.y);
       const float t_ = tstage ? tsm[b * W + x] : __ldg(&tg[(size_t)y * W + x]);
       const float d = I_ - t_;
@@ -229,9 +271,10 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
     else F::template rest<false>(u, w, buf, tw);
     // row and base re-derived from the block index (fewer values live across the transform)
     float2* hv = V + (size_t)blockIdx.y * bl.H * N;
-    reg::for_each<N, F::C, NB, T>(w, [&](int b, int a, float2& val) {
+    const unsigned MHF = (unsigned)(N / F::C) * (unsigned)bl.H;
+    reg::for_each_jr<N, F::C, NB, T>(w, [&](int b, int j, int r, float2& val) {
       const int y = blockIdx.x * NB + b;
-      if (y < bl.H) hv[((size_t)(a / CB) * bl.H + y) * CB + (a % CB)] = val;
+      if (y < bl.H) hv[blk_base<CB>(j, y, bl.H) + (unsigned)r * MHF] = val;
     });
   }
   // at the end, where no transform state is live
@@ -270,7 +313,7 @@ __device__ __forceinline__ bool rows_inband(const BlasmDev& bl, const TFConst& t
 
 // INBAND: every bin of every channel and plane lies inside the band and there is no
 // aperture (checked on the host), so the masked evaluation of H is not even compiled.
-template <int N, int R0, int R1, int R2, int NB, int T, int MINB, bool INBAND>
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB, bool INBAND, bool CA>
 __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_constant__ BlasmDev bl,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ Y,
@@ -287,9 +330,10 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
   const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
   const float4* src = reinterpret_cast<const float4*>(Y + (size_t)c * H * Nx + (size_t)kb * H * CB);
   float4 v[F::GA::MB][F::A];
-  reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
-    const int y = a - oy;
-    return (y >= 0 && y < H) ? __ldg(&src[y * NB + b]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
+    int y;
+    return in_window<N, F::A, CA>(j, r, oy, H, y) ? __ldg(&src[y * NB + b])
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
   });
   // the spectrum is parked in thread-private shared-memory slots (one 16-byte load per
   // element per plane) so that the inverse passes get the registers
@@ -324,14 +368,14 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
     float4 u[I::GC::MB][I::C];
     if constexpr (DB) I::rest2(Z, u, buf4, by, tw); else I::rest(Z, u, buf4, tw);
     float4* dst = reinterpret_cast<float4*>(V + (size_t)(l * C + c) * H * Nx + (size_t)kb * H * CB);
-    reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float4& val) {
-      const int y = a - oy;
-      if (y >= 0 && y < H) dst[y * NB + b] = val;
+    reg::for_each_jr<N, I::C, NB, T>(u, [&](int b, int j, int r, float4& val) {
+      int y;
+      if (in_window<N, I::C, CA>(j, r, oy, H, y)) dst[y * NB + b] = val;
     });
   }
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T, int MINB, bool INBAND>
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB, bool INBAND, bool CA>
 __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_constant__ BlasmDev bl,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ G,
@@ -359,9 +403,10 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
       for (int i = threadIdx.x; i * 128 < H * CB * 8; i += T) prefetch_l2(nxt + i * 128);
     }
     float4 v[F::GA::MB][F::A];
-    reg::first_from<N, F::A, NB, T, false>(v, [&](int b, int a) {
-      const int y = a - oy;
-      return (y >= 0 && y < H) ? __ldg(&src[y * NB + b]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
+      int y;
+      return in_window<N, F::A, CA>(j, r, oy, H, y) ? __ldg(&src[y * NB + b])
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
     });
     float4 S[F::GC::MB][F::C];
     if constexpr (DB) F::rest2(v, S, buf4, by, tw); else F::rest(v, S, buf4, tw);
@@ -392,9 +437,9 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
   float4 u[I::GC::MB][I::C];
   if constexpr (DB) I::rest2(acc, u, buf4, by, tw); else I::rest(acc, u, buf4, tw);
   float4* dst = reinterpret_cast<float4*>(D + (size_t)c * H * Nx + (size_t)kb * H * CB);
-  reg::for_each<N, I::C, NB, T>(u, [&](int b, int a, float4& val) {
-    const int y = a - oy;
-    if (y >= 0 && y < H) dst[y * NB + b] = val;
+  reg::for_each_jr<N, I::C, NB, T>(u, [&](int b, int j, int r, float4& val) {
+    int y;
+    if (in_window<N, I::C, CA>(j, r, oy, H, y)) dst[y * NB + b] = val;
   });
 }
 
@@ -413,8 +458,9 @@ inline cudaError_t reg_set_smem(K kernel, size_t bytes, int resident) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)pct);
 }
 
-template <int N, int R0, int R1, int R2, int NB, int CB, int T>
-cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, cudaStream_t s) {
+template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool CA>
+cudaError_t reg_rows_launch_ca(int kind, const cgh_plan* p, const SpecRowArgs* a,
+                               const BlasmDev& bl, cudaStream_t s) {
   using P = RegPlan<N, R0, R1, R2, NB, T>;
   constexpr size_t smem_db =
       P::SMEM + (P::db_rows_fits(CGH_REG_MINB(T), 0) ? sizeof(float2) * (size_t)P::BUF2 : 0);
@@ -423,11 +469,10 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
   constexpr size_t smem_acc = P::SMEM + (db_acc ? sizeof(float2) * (size_t)P::BUF2 : 0);
   dim3 grid((p->H + NB - 1) / NB, a->batches);
   const float2* tw = p->fx.tw;
-  const BlasmDev& bl = a->bl ? *a->bl : p->bl;
   cudaError_t e = cudaSuccess;
   switch (kind) {
     case SPEC_ROWS_PAD_FWD: {
-      auto k = kr_rows_pad_fwd<N, R0, R1, R2, NB, CB, T>;
+      auto k = kr_rows_pad_fwd<N, R0, R1, R2, NB, CB, T, CA>;
       e = reg_set_smem(k, smem_db, CGH_REG_MINB(T));
       if (e != cudaSuccess) return e;
       prof_begin(KID_ROWS_PAD_FWD, s);
@@ -436,8 +481,8 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
       break;
     }
     case SPEC_ROWS_INV_CROP: {
-      auto k = a->accumulate ? kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T, true>
-                             : kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T, false>;
+      auto k = a->accumulate ? kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T, true, CA>
+                             : kr_rows_inv_crop<N, R0, R1, R2, NB, CB, T, false, CA>;
       const bool stage = a->accumulate && p->W % 2 == 0 &&
                          (reinterpret_cast<uintptr_t>(a->out) & 15u) == 0;
       const int accum = a->accumulate ? (stage ? 1 : 2) : 0;
@@ -453,10 +498,10 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
     default: {
       const int tstage = (p->W % 4 == 0 && (reinterpret_cast<uintptr_t>(a->target) & 15u) == 0);
       const bool general = !tstage || bl.loss_kind != 0;
-      auto k = a->want_grad ? (general ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, true, true>
-                                       : kr_rows_loss<N, R0, R1, R2, NB, CB, T, true, false>)
-                            : (general ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, false, true>
-                                       : kr_rows_loss<N, R0, R1, R2, NB, CB, T, false, false>);
+      auto k = a->want_grad ? (general ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, true, true, CA>
+                                       : kr_rows_loss<N, R0, R1, R2, NB, CB, T, true, false, CA>)
+                            : (general ? kr_rows_loss<N, R0, R1, R2, NB, CB, T, false, true, CA>
+                                       : kr_rows_loss<N, R0, R1, R2, NB, CB, T, false, false, CA>);
       constexpr bool db = P::db_rows_fits(CGH_REG_MINB(T), rows_stage_bytes<N, NB>());
       const size_t smem = P::SMEM + (db ? sizeof(float2) * (size_t)P::BUF2 : 0) +
                           (tstage ? sizeof(float) * (size_t)NB * p->W : 0);
@@ -472,13 +517,24 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
   return cudaGetLastError();
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T, int MINB>
-cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, const float2* in,
-                            float2* out, cudaStream_t s) {
+// The row kernels come in two forms: with the image window aligned to the passes' geometry
+// (W = N / 2, ox = N / 4: pad factor 2, compile-time crop tests) and the general one.
+template <int N, int R0, int R1, int R2, int NB, int CB, int T>
+cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, cudaStream_t s) {
+  const BlasmDev& bl = a->bl ? *a->bl : p->bl;
+  if (2 * bl.W == N && 4 * bl.ox == N)
+    return reg_rows_launch_ca<N, R0, R1, R2, NB, CB, T, true>(kind, p, a, bl, s);
+  return reg_rows_launch_ca<N, R0, R1, R2, NB, CB, T, false>(kind, p, a, bl, s);
+}
+
+template <int N, int R0, int R1, int R2, int NB, int T, int MINBF, int MINBB, bool CA>
+cudaError_t reg_cols_launch_ca(int kind, const cgh_plan* p, const BlasmDev& bl, const float2* in,
+                               float2* out, cudaStream_t s) {
   using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
   static_assert(P::F::C == P::I::A, "slot layout shared by the forward end and inverse start");
+  constexpr int MINB = MINBF;  // in-band forward kernel
   constexpr size_t smem = P::db_fits(MINB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
-  const BlasmDev& bl = blp ? *blp : p->bl;
+  constexpr size_t smem_b = P::db_fits(MINBB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
   dim3 grid(bl.Nx / (2 * NB), p->C);
   const float2* tw = p->fy.tw;
   cudaError_t e = cudaSuccess;
@@ -489,23 +545,38 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, co
       all_in = all_in && t.kx_max >= bl.Nx / 2 && t.ky_max >= N / 2;
     }
   if (kind == SPEC_COLS_FWD_PLANES) {
-    auto k = all_in ? kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, true>
-                    : kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
-    e = reg_set_smem(k, smem, MINB);
+    // MINBF applies to the in-band form (the masked one keeps the general residency)
+    auto k = all_in ? kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, true, CA>
+                    : kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINBB, false, CA>;
+    const size_t sm = all_in ? smem : smem_b;
+    e = reg_set_smem(k, sm, all_in ? MINB : MINBB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
-    k<<<grid, T, smem, s>>>(bl, tw, in, out);
+    k<<<grid, T, sm, s>>>(bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
-    auto k = all_in ? kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, true>
-                    : kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINB, false>;
-    e = reg_set_smem(k, smem, MINB);
+    auto k = all_in ? kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINBB, true, CA>
+                    : kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINBB, false, CA>;
+    e = reg_set_smem(k, smem_b, MINBB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
-    k<<<grid, T, smem, s>>>(bl, tw, in, out);
+    k<<<grid, T, smem_b, s>>>(bl, tw, in, out);
     prof_end(KID_COLS_BWD_PLANES, s);
   }
   return cudaGetLastError();
+}
+
+// Column kernels, like the row kernels, come with the image window aligned (H = N / 2,
+// oy = N / 4) and in the general form.
+// MINBA: resident CTAs per SM of the aligned-window, in-band forward kernel (its dead cropped
+// outputs and known zero inputs free registers, so it can fit more CTAs than the others).
+template <int N, int R0, int R1, int R2, int NB, int T, int MINB, int MINBA>
+cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, const float2* in,
+                            float2* out, cudaStream_t s) {
+  const BlasmDev& bl = blp ? *blp : p->bl;
+  if (2 * bl.H == N && 4 * bl.oy == N)
+    return reg_cols_launch_ca<N, R0, R1, R2, NB, T, MINBA, MINB, true>(kind, p, bl, in, out, s);
+  return reg_cols_launch_ca<N, R0, R1, R2, NB, T, MINB, MINB, false>(kind, p, bl, in, out, s);
 }
 
 }  // namespace cgh
@@ -519,8 +590,11 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, co
   }
 //   column entries: NB float4 slots per CTA, i.e. CB = 2 NB columns; MINB resident CTAs per
 //   SM the registers are sized for.
-#define CGH_COL_SPEC(N, R0, R1, R2, NB, T, MINB)                                            \
+#define CGH_COL_SPEC(N, R0, R1, R2, NB, T, MINB) CGH_COL_SPEC_A(N, R0, R1, R2, NB, T, MINB, MINB)
+//   ... with MINBA resident CTAs for the aligned-window forward kernel
+#define CGH_COL_SPEC_A(N, R0, R1, R2, NB, T, MINB, MINBA)                                    \
   if (N_ == N && CB_ == 2 * (NB)) {                                                         \
-    if (!dry) *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T, MINB>(kind, p, bl, in, out, s); \
+    if (!dry)                                                                               \
+      *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T, MINB, MINBA>(kind, p, bl, in, out, s); \
     return true;                                                                            \
   }

@@ -11,6 +11,6 @@ bool spec_rows_a(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const Sp
 bool spec_cols_a(int kind, int N_, int CB_, const cgh_plan* p, const BlasmDev* bl,
                  const float2* in, float2* out,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_COL_SPEC(2160, 15, 12, 12, 1, 192, 2)
+  CGH_COL_SPEC_A(2160, 15, 12, 12, 1, 192, 2, 2)
   return false;
 }

@@ -101,6 +101,24 @@ __device__ __forceinline__ void first_from(E (&v)[Geo<N, R, NB, T>::MB][R], F&& 
   }
 }
 
+// Same with the functor called as f(b, j, r) for position j + r N/R, r a constant after
+// unrolling: terms of an address that depend only on (b, j) are then computed once per
+// butterfly, the r-dependent part folds into a constant or one multiply-add.
+template <int N, int R, int NB, int T, bool INV, class E, class F>
+__device__ __forceinline__ void first_from_jr(E (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) {
+      const int b = (int)((unsigned)q % NB), j = (int)((unsigned)q / NB);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i][r] = f(b, j, r);
+      DFT<R, INV>::run(v[i]);
+    }
+  }
+}
+
 // First pass (Ns = 1) on values already in registers at positions j + r N/R.
 template <int N, int R, int NB, int T, bool INV, class E>
 __device__ __forceinline__ void first_in_regs(E (&v)[Geo<N, R, NB, T>::MB][R]) {
@@ -179,6 +197,21 @@ __device__ __forceinline__ void for_each(E (&v)[Geo<N, R, NB, T>::MB][R], F&& f)
       const int b = q % NB, j = q / NB;
 #pragma unroll
       for (int r = 0; r < R; ++r) f(b, j + r * G::M, v[i][r]);
+    }
+  }
+}
+
+// Same visit with f(b, j, r, value&) for position j + r N/R (see first_from_jr).
+template <int N, int R, int NB, int T, class E, class F>
+__device__ __forceinline__ void for_each_jr(E (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
+  using G = Geo<N, R, NB, T>;
+#pragma unroll
+  for (int i = 0; i < G::MB; ++i) {
+    const int q = threadIdx.x + i * T;
+    if (valid<N, R, NB, T>(q)) {
+      const int b = (int)((unsigned)q % NB), j = (int)((unsigned)q / NB);
+#pragma unroll
+      for (int r = 0; r < R; ++r) f(b, j, r, v[i][r]);
     }
   }
 }
