@@ -1405,6 +1405,13 @@ def main():
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
+    # the (Gaussian, 16x16 tile) list length the timed steps binned (read before the context
+    # run below: re-tuning the plan re-attaches its workspace, which clears the status words)
+    tile_pairs = plan.status()["pairs"]
+    # the sweeps' work at the final parameters, counted on the device with the kernels' own
+    # box geometry (lane slots evaluated against pairs that pass the cutoff)
+    sweep = plan.raster_stats({k: v.detach() for k, v in params.items()})
+
     # ---- context: the same steps with every plane propagated through the FFT passes (the
     # plane at 0 mm too), i.e. without the pixel-domain path for identity planes
     full_prop = None
@@ -1489,9 +1496,17 @@ def main():
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
             "gpu_launches": launches, "kernels": per_kernel, "clocks": clk,
             # rasteriser work after the run's steps: the (Gaussian, 16x16 tile) list the
-            # kernels walk, and the estimated (pixel, Gaussian) pairs above the cutoff
+            # kernels walk, the lane slots each sweep evaluates and the (pixel, Gaussian) pairs
+            # that pass the cutoff (device counts, cgh_raster_stats), and the host estimate of
+            # the latter
             "raster_pairs": {
-                "tile_list": plan.status()["pairs"],
+                "tile_list": tile_pairs,
+                "contributing_pairs": sweep["contributing_pairs"],
+                "fwd_lane_slots": sweep["fwd_lane_slots"],
+                "bwd_lane_slots": sweep["bwd_lane_slots"],
+                "region_pairs": sweep["region_pairs"],
+                "fwd_slots_per_contributing": sweep["fwd_lane_slots"] / max(1, sweep["contributing_pairs"]),
+                "bwd_slots_per_contributing": sweep["bwd_lane_slots"] / max(1, sweep["contributing_pairs"]),
                 "pixel_pairs_est": raster_pairs({k: v.detach().cpu().numpy()
                                                  for k, v in params.items()}, w.cutoff)},
             "torch_cufft_blasm": torch_blasm_ms(w, dev) if not args.no_extras else None,

@@ -170,6 +170,20 @@ cgh_status cgh_plan_status(cgh_plan* plan, int64_t* pairs_needed, int32_t* overf
 cgh_status cgh_raster_fwd(cgh_plan* plan, const cgh_params* params, void* U_out,
                           void* stream);
 
+/* Work counters of the two rasteriser sweeps (a diagnostic; the paper has no counterpart):
+ * bins `params` as cgh_raster_fwd does, then counts with the kernels' own box geometry, and
+ * returns (blocking on `stream`) six int64 in the HOST array counts_out:
+ *   [0] lane slots the forward sweep evaluates (32 per 8x4 pixel block per listed Gaussian
+ *       whose box touches it),
+ *   [1] (pixel, Gaussian) pairs with alpha G >= cutoff (the pairs that contribute),
+ *   [2] lane slots the backward sweep evaluates (per Gaussian and 32x32 region, the box's
+ *       pixels in the region rounded up to whole warps of 32),
+ *   [3] (Gaussian, 32x32 region) pairs of the backward, [4] (Gaussian, 16x16 tile) entries,
+ *   [5] tiles whose list overflowed the capacity (not counted in [0]..[4]).
+ * Uses the plan's workspace like every other call (its loss partials are overwritten). */
+cgh_status cgh_raster_stats(cgh_plan* plan, const cgh_params* params, int64_t* counts_out,
+                            void* stream);
+
 /* Forward rasterisation that allocates nothing and needs no plan.  The paper has no
  * counterpart: this exists for callers that may not allocate device memory -- e.g. an
  * application that reserves all device memory at start-up, or a latency-critical loop where

@@ -53,6 +53,7 @@ class _AdamGroup(ctypes.Structure):
 EXPORTS = ("cgh_plan_create", "cgh_plan_destroy", "cgh_plan_workspace_bytes",
            "cgh_plan_set_workspace", "cgh_plan_set_tuning", "cgh_plan_get_tuning",
            "cgh_plan_band_limits", "cgh_plan_status", "cgh_raster_fwd", "cgh_raster_bwd",
+           "cgh_raster_stats",
            "cgh_blasm_fwd", "cgh_blasm_bwd", "cgh_intensity_loss", "cgh_forward_loss",
            "cgh_intensity", "cgh_intensity_bwd", "cgh_plan_identity_planes",
            "cgh_batch_step_persistent", "cgh_batch_persistent_status", "cgh_batch_persistent_test",
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True):
     lib.cgh_raster_fwd.argtypes = [vp, ctypes.POINTER(_Params), vp, vp]
     lib.cgh_raster_fwd_noalloc.argtypes = [i32, i32, i32, f32, ctypes.POINTER(_Params), vp, vp]
     lib.cgh_raster_bwd.argtypes = [vp, ctypes.POINTER(_Params), vp, ctypes.POINTER(_Grads), vp]
+    lib.cgh_raster_stats.argtypes = [vp, ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_int64), vp]
     lib.cgh_blasm_fwd.argtypes = [vp, vp, vp, vp]
     lib.cgh_blasm_bwd.argtypes = [vp, vp, vp, vp]
     lib.cgh_intensity_loss.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -388,6 +390,17 @@ class Plan:
         _check(_lib.cgh_raster_fwd(self._h, ctypes.byref(prm), ctypes.c_void_p(U.data_ptr()),
                                    ctypes.c_void_p(_stream(stream))), "cgh_raster_fwd")
         return U
+
+    def raster_stats(self, params, stream=None) -> dict:
+        """cgh_raster_stats: work counters of the forward and backward sweeps."""
+        prm = self._params(params)
+        c = (ctypes.c_int64 * 6)()
+        with torch.cuda.device(self.device):
+            _check(_lib.cgh_raster_stats(self._h, ctypes.byref(prm), c,
+                                         ctypes.c_void_p(_stream(stream))), "cgh_raster_stats")
+        keys = ("fwd_lane_slots", "contributing_pairs", "bwd_lane_slots", "region_pairs",
+                "tile_pairs", "overflow_tiles")
+        return {k: int(c[i]) for i, k in enumerate(keys)}
 
     def raster_bwd(self, params, dU, grads=None, stream=None) -> Dict[str, torch.Tensor]:
         prm = self._params(params)

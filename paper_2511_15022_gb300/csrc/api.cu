@@ -445,6 +445,21 @@ extern "C" cgh_status cgh_raster_fwd(cgh_plan* plan, const cgh_params* params, v
   return CGH_OK;
 }
 
+extern "C" cgh_status cgh_raster_stats(cgh_plan* plan, const cgh_params* params,
+                                       int64_t* counts_out, void* stream) {
+  CGH_CHECK(check_call(plan, params));
+  if (!params || !counts_out) return fail(CGH_ERR_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  // the six counters live in the loss-partial slots (at least 1024 floats, 256-byte aligned)
+  unsigned long long* dev = reinterpret_cast<unsigned long long*>(plan->ws + plan->off_loss);
+  unsigned long long host[6];
+  CGH_TRY(launch_raster_stats(plan, params, dev, s), "cgh_raster_stats");
+  CGH_TRY(cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s), "cgh_raster_stats");
+  CGH_TRY(cudaStreamSynchronize(s), "cgh_raster_stats");
+  for (int k = 0; k < 6; ++k) counts_out[k] = (int64_t)host[k];
+  return CGH_OK;
+}
+
 extern "C" cgh_status cgh_raster_bwd(cgh_plan* plan, const cgh_params* params, const void* dU,
                                      const cgh_grads* grads, void* stream) {
   CGH_CHECK(check_call(plan, params));

@@ -154,6 +154,9 @@ cudaError_t launch_raster_fwd(cgh_plan* p, const cgh_params* prm, float2* U, cud
 cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* dU,
                               const cgh_grads* g, cudaStream_t s, bool rebin,
                               const float* grad_scale = nullptr);
+// bins `prm` and counts the sweeps' work into out[6] (device, cgh_raster_stats)
+cudaError_t launch_raster_stats(cgh_plan* p, const cgh_params* prm, unsigned long long* out,
+                                cudaStream_t s);
 // blasm.cu
 // The column passes and the loss pass take a plane map (NULL: every plane, &p->bl).
 cudaError_t launch_rows_pad_fwd(cgh_plan* p, const float2* in, float2* half, int batches,

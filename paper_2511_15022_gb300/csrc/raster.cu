@@ -187,3 +187,83 @@ cudaError_t launch_raster_bwd(cgh_plan* p, const cgh_params* prm, const float2* 
   }
   return cudaGetLastError();
 }
+
+// ------------------------------------------------------------------ sweep work counters
+// Diagnostics of the two sweeps over the binning of `params` (not on the timed path).  One
+// CTA per 16x16 tile; each thread takes entries of the tile's list and counts, with the same
+// box geometry the kernels use:
+//   out[0] forward lane slots: 32 per 8x4 warp block the Gaussian's box touches
+//          (raster_fwd_tile visits exactly those (block, Gaussian) pairs);
+//   out[1] (pixel, Gaussian) pairs that pass the cutoff (alpha G >= cutoff, the test both
+//          sweeps take; tiles partition the pixels, so each pair is counted once);
+//   out[2] backward lane slots: for the Gaussian's home tile in its 32x32 region, the box's
+//          pixels inside the region rounded up to whole warps (raster_bwd_region sweeps
+//          exactly those);
+//   out[3] (Gaussian, region) pairs of the backward;  out[4] (Gaussian, tile) list entries.
+// Tiles whose list overflowed the capacity are not counted (out[5] = their number).
+__global__ void __launch_bounds__(256) k_raster_stats(RasterConsts rc, const float4* __restrict__ rec,
+                                                      const int4* __restrict__ rect,
+                                                      const int* __restrict__ tile_start,
+                                                      const int* __restrict__ pairs,
+                                                      unsigned long long* __restrict__ out) {
+  const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * rc.tiles_x + tx;
+  const int start = tile_start[tile], end = tile_start[tile + 1];
+  unsigned long long fwd = 0, hits = 0, bwd = 0, regions = 0, entries = 0;
+  if ((long long)end > rc.cap) {
+    if (threadIdx.x == 0) atomicAdd(&out[5], 1ull);
+    return;  // CTA-uniform: no barrier follows
+  }
+  const int ox = tx * CGH_TILE, oy = ty * CGH_TILE;
+  const int STX = tx / 2, STY = ty / 2;
+  for (int i = start + (int)threadIdx.x; i < end; i += blockDim.x) {
+    const int gid = pairs[i];
+    const float4* g = rec + (size_t)gid * CGH_REC_F4;
+    const float4 r0 = g[0], r1 = g[1], bb = g[2];
+    const int4 r = rect[gid];
+    ++entries;
+    // forward: the warp blocks of this tile the box touches
+    for (int w = 0; w < 8; ++w) {
+      const float x0 = (float)(ox + (w & 1) * 8), y0 = (float)(oy + (w >> 1) * 4);
+      if (bb.y >= x0 && bb.x <= x0 + 7.f && bb.w >= y0 && bb.z <= y0 + 3.f) fwd += 32;
+    }
+    // pairs passing the cutoff inside this tile
+    for (int py = oy; py < oy + CGH_TILE && py < rc.H; ++py)
+      for (int px = ox; px < ox + CGH_TILE && px < rc.W; ++px) {
+        const float p2 = gauss_power(r0, r1, (float)px - r0.x, (float)py - r0.y);
+        if (p2 >= r1.y) ++hits;
+      }
+    // backward: counted once per region, from the Gaussian's home tile
+    if (tx == max(r.x, 2 * STX) && ty == max(r.y, 2 * STY)) {
+      const int rx = STX * kSuper, ry = STY * kSuper;
+      const int x0 = (int)ceilf(fmaxf(bb.x, (float)rx)), x1 = (int)floorf(fminf(bb.y, (float)(rx + kSuper - 1)));
+      const int y0 = (int)ceilf(fmaxf(bb.z, (float)ry)), y1 = (int)floorf(fminf(bb.w, (float)(ry + kSuper - 1)));
+      if (x0 <= x1 && y0 <= y1) {
+        const int npx = (x1 - x0 + 1) * (y1 - y0 + 1);
+        bwd += (unsigned long long)((npx + 31) / 32) * 32;
+        ++regions;
+      }
+    }
+  }
+  unsigned long long v[5] = {fwd, hits, bwd, regions, entries};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    unsigned long long x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&out[k], x);
+  }
+}
+
+cudaError_t launch_raster_stats(cgh_plan* p, const cgh_params* prm, unsigned long long* out,
+                                cudaStream_t s) {
+  cudaError_t e = bin(p, prm, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(out, 0, sizeof(unsigned long long) * 6, s);
+  if (e != cudaSuccess) return e;
+  RasterConsts rc = make_consts(p, prm->N);
+  dim3 grid(p->tiles_x, p->tiles_y);
+  k_raster_stats<<<grid, 256, 0, s>>>(rc, (const float4*)(p->ws + p->off_rec),
+                                      (const int4*)(p->ws + p->off_rect),
+                                      (const int*)(p->ws + p->off_tile_start),
+                                      (const int*)(p->ws + p->off_pairs), out);
+  return cudaGetLastError();
+}
