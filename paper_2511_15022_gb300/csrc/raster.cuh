@@ -363,89 +363,94 @@ __device__ __forceinline__ int stage_batch(const RasterConsts& rc, const float4*
 // ((w & 1) 8, (w >> 1) 4) of the tile.  When a batch is staged, the thread that staged a
 // Gaussian also marks which warp blocks its box touches; each warp then compacts its own
 // list with ballots and visits only those Gaussians.
-// One tile (tx, ty) by a CTA of 256 threads; shared memory: srec[256 * CGH_REC_F4],
-// smask[256], slist[8][256] (+ red[8] with LOSS).  LOSS: the identity planes' loss (and
-// seed) of IdentLoss on the finished pixels, whose values are still in registers.
-template <int C, bool LOSS = false>
-__device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
-                                                const float4* __restrict__ rec,
-                                                const int4* __restrict__ rect,
-                                                const int* __restrict__ tile_start,
-                                                const int* __restrict__ pairs,
-                                                float2* __restrict__ U, int tx, int ty,
-                                                float4* srec, unsigned char* smask,
-                                                unsigned char (*slist)[256],
-                                                const IdentLoss* il = nullptr,
-                                                float* red = nullptr) {
-  const int tile = ty * rc.tiles_x + tx;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wx0 = tx * CGH_TILE + (warp & 1) * 8, wy0 = ty * CGH_TILE + (warp >> 1) * 4;
-  const int px = wx0 + (lane & 7), py = wy0 + (lane >> 3);
-  const float fpx = (float)px, fpy = (float)py;
-  const float fox = (float)(tx * CGH_TILE), foy = (float)(ty * CGH_TILE);
-  const int start = CGH_WS_LOAD(&tile_start[tile]), end = CGH_WS_LOAD(&tile_start[tile + 1]);
-  const bool exhaustive = (long long)end > rc.cap;
-  const int count = exhaustive ? rc.N : end - start;
-  float accr[C], acci[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) { accr[c] = 0.f; acci[c] = 0.f; }
-  for (int base = 0; base < count; base += 256) {
-    __syncthreads();
-    const int nb = stage_batch(rc, rec, rect, pairs, start, count, exhaustive, base, tx, ty,
-                               srec, nullptr);
-    if (threadIdx.x < nb) {
-      // warp blocks (2 columns x 4 rows of the tile) the staged box touches
-      const float4 bb = srec[threadIdx.x * CGH_REC_F4 + 2];
-      unsigned m = 0;
-#pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        const float x0 = fox + (float)((w & 1) * 8), y0 = foy + (float)((w >> 1) * 4);
-        if (bb.y >= x0 && bb.x <= x0 + 7.f && bb.w >= y0 && bb.z <= y0 + 3.f) m |= 1u << w;
-      }
-      smask[threadIdx.x] = (unsigned char)m;
-    }
-    __syncthreads();
-    int cnt = 0;
-    for (int k = 0; k < nb; k += 32) {
-      const int i = k + lane;
-      const bool mine = i < nb && ((smask[i] >> warp) & 1u);
-      const unsigned b = __ballot_sync(0xffffffffu, mine);
-      if (mine) slist[warp][cnt + __popc(b & ((1u << lane) - 1u))] = (unsigned char)i;
-      cnt += __popc(b);
-    }
-    __syncwarp();
-    // contribution of the Gaussian whose record starts at srec[j] (power p2 >= its cutoff)
-    auto splat = [&](int j, float p2, float alpha) {
-      const float a = fminf(kAlphaCap, alpha * pow2_clamped(p2));
-      const float4 r3 = srec[j + 3];
-      const float4 r4 = srec[j + 4];
-      const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
-      const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        accr[c] = fmaf(a, Ac[c], accr[c]);
-        acci[c] = fmaf(a, Bc[c], acci[c]);
-      }
-    };
-    // the warp's Gaussians two at a time, in list order: both records' geometry is read
-    // before either power is tested (more loads in flight, half the loop overhead)
-    int t = 0;
-    for (; t + 2 <= cnt; t += 2) {
-      const int j0 = slist[warp][t] * CGH_REC_F4, j1 = slist[warp][t + 1] * CGH_REC_F4;
-      const float4 a0 = srec[j0], b0 = srec[j0 + 1];
-      const float4 a1 = srec[j1], b1 = srec[j1 + 1];
-      const float p0 = gauss_power(a0, b0, fpx - a0.x, fpy - a0.y);
-      const float p1 = gauss_power(a1, b1, fpx - a1.x, fpy - a1.y);
-      if (p0 >= b0.y) splat(j0, p0, b0.z);
-      if (p1 >= b1.y) splat(j1, p1, b1.z);
-    }
-    if (t < cnt) {
-      const int j0 = slist[warp][t] * CGH_REC_F4;
-      const float4 a0 = srec[j0], b0 = srec[j0 + 1];
-      const float p0 = gauss_power(a0, b0, fpx - a0.x, fpy - a0.y);
-      if (p0 >= b0.y) splat(j0, p0, b0.z);
-    }
+
+// Pixel of this thread in tile (tx, ty) and the tile's origin.
+struct FwdPixel {
+  int px, py;
+  float fpx, fpy, fox, foy;
+  __device__ __forceinline__ FwdPixel(int tx, int ty) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    px = tx * CGH_TILE + (warp & 1) * 8 + (lane & 7);
+    py = ty * CGH_TILE + (warp >> 1) * 4 + (lane >> 3);
+    fpx = (float)px; fpy = (float)py;
+    fox = (float)(tx * CGH_TILE); foy = (float)(ty * CGH_TILE);
   }
+};
+
+// One staged batch of nb records in srec (thread i < nb staged record i and may read it back
+// without a barrier): warp masks, a barrier, per-warp compaction, then the warp's Gaussians
+// accumulated into accr / acci.
+template <int C>
+__device__ __forceinline__ void fwd_sweep_batch(const FwdPixel& q, const float4* srec, int nb,
+                                                unsigned char* smask,
+                                                unsigned char (*slist)[256], float (&accr)[C],
+                                                float (&acci)[C]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if ((int)threadIdx.x < nb) {
+    // warp blocks (2 columns x 4 rows of the tile) the staged box touches
+    const float4 bb = srec[threadIdx.x * CGH_REC_F4 + 2];
+    unsigned m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const float x0 = q.fox + (float)((w & 1) * 8), y0 = q.foy + (float)((w >> 1) * 4);
+      if (bb.y >= x0 && bb.x <= x0 + 7.f && bb.w >= y0 && bb.z <= y0 + 3.f) m |= 1u << w;
+    }
+    smask[threadIdx.x] = (unsigned char)m;
+  }
+  __syncthreads();
+  int cnt = 0;
+  for (int k = 0; k < nb; k += 32) {
+    const int i = k + lane;
+    const bool mine = i < nb && ((smask[i] >> warp) & 1u);
+    const unsigned b = __ballot_sync(0xffffffffu, mine);
+    if (mine) slist[warp][cnt + __popc(b & ((1u << lane) - 1u))] = (unsigned char)i;
+    cnt += __popc(b);
+  }
+  __syncwarp();
+  // contribution of the Gaussian whose record starts at srec[j] (power p2 >= its cutoff)
+  auto splat = [&](int j, float p2, float alpha) {
+    const float a = fminf(kAlphaCap, alpha * pow2_clamped(p2));
+    const float4 r3 = srec[j + 3];
+    const float4 r4 = srec[j + 4];
+    const float Ac[4] = {r3.x, r3.z, r4.x, r4.z};
+    const float Bc[4] = {r3.y, r3.w, r4.y, r4.w};
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      accr[c] = fmaf(a, Ac[c], accr[c]);
+      acci[c] = fmaf(a, Bc[c], acci[c]);
+    }
+  };
+  // the warp's Gaussians two at a time, in list order: both records' geometry is read
+  // before either power is tested (more loads in flight, half the loop overhead)
+  int t = 0;
+  for (; t + 2 <= cnt; t += 2) {
+    const int j0 = slist[warp][t] * CGH_REC_F4, j1 = slist[warp][t + 1] * CGH_REC_F4;
+    const float4 a0 = srec[j0], b0 = srec[j0 + 1];
+    const float4 a1 = srec[j1], b1 = srec[j1 + 1];
+    const float p0 = gauss_power(a0, b0, q.fpx - a0.x, q.fpy - a0.y);
+    const float p1 = gauss_power(a1, b1, q.fpx - a1.x, q.fpy - a1.y);
+    if (p0 >= b0.y) splat(j0, p0, b0.z);
+    if (p1 >= b1.y) splat(j1, p1, b1.z);
+  }
+  if (t < cnt) {
+    const int j0 = slist[warp][t] * CGH_REC_F4;
+    const float4 a0 = srec[j0], b0 = srec[j0 + 1];
+    const float p0 = gauss_power(a0, b0, q.fpx - a0.x, q.fpy - a0.y);
+    if (p0 >= b0.y) splat(j0, p0, b0.z);
+  }
+}
+
+// The finished pixel: U stored and, with LOSS, the identity planes' loss (and seed) of `il`
+// on it (U(d_l) = U(0) for those planes): per plane l and channel c, d = |U|^2 - T_l and the
+// weight w of the loss (1, or 1 + M + T^2 for L_recon, Sec. 3.2); the tile's sum of w d^2 is
+// one loss partial, the seed gscale sum_l w d U the loss row pass would form.  Ends with a
+// barrier when LOSS.
+template <int C, bool LOSS>
+__device__ __forceinline__ void fwd_epilogue(const RasterConsts& rc, const FwdPixel& q, int tile,
+                                             const float (&accr)[C], const float (&acci)[C],
+                                             float2* __restrict__ U, const IdentLoss* il,
+                                             float* red) {
+  const int px = q.px, py = q.py;
   const bool inside = px < rc.W && py < rc.H;
   const size_t plane = (size_t)rc.H * rc.W, o = (size_t)py * rc.W + px;
   if (inside) {
@@ -453,9 +458,6 @@ __device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
     for (int c = 0; c < C; ++c) U[c * plane + o] = make_float2(accr[c], acci[c]);
   }
   if constexpr (LOSS) {
-    // identity planes (U(d_l) = U(0)): per plane l and channel c, d = |U|^2 - T_l and the
-    // weight w of the loss (1, or 1 + M + T^2 for L_recon, Sec. 3.2); the tile's sum of
-    // w d^2 is one loss partial, the seed gscale sum_l w d U the loss row pass would form
     float acc = 0.f;
     if (inside) {
 #pragma unroll
@@ -482,6 +484,7 @@ __device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
         }
       }
     }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = 16; k > 0; k >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, k);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
@@ -491,6 +494,37 @@ __device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
       il->partials[tile] = tot;
     }
   }
+}
+
+// One tile (tx, ty) by a CTA of 256 threads; shared memory: srec[256 * CGH_REC_F4],
+// smask[256], slist[8][256] (+ red[8] with LOSS).  LOSS: the identity planes' loss (and
+// seed) of IdentLoss on the finished pixels, whose values are still in registers.
+template <int C, bool LOSS = false>
+__device__ __forceinline__ void raster_fwd_tile(const RasterConsts& rc,
+                                                const float4* __restrict__ rec,
+                                                const int4* __restrict__ rect,
+                                                const int* __restrict__ tile_start,
+                                                const int* __restrict__ pairs,
+                                                float2* __restrict__ U, int tx, int ty,
+                                                float4* srec, unsigned char* smask,
+                                                unsigned char (*slist)[256],
+                                                const IdentLoss* il = nullptr,
+                                                float* red = nullptr) {
+  const int tile = ty * rc.tiles_x + tx;
+  const FwdPixel q(tx, ty);
+  const int start = CGH_WS_LOAD(&tile_start[tile]), end = CGH_WS_LOAD(&tile_start[tile + 1]);
+  const bool exhaustive = (long long)end > rc.cap;
+  const int count = exhaustive ? rc.N : end - start;
+  float accr[C], acci[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) { accr[c] = 0.f; acci[c] = 0.f; }
+  for (int base = 0; base < count; base += 256) {
+    __syncthreads();
+    const int nb = stage_batch(rc, rec, rect, pairs, start, count, exhaustive, base, tx, ty,
+                               srec, nullptr);
+    fwd_sweep_batch<C>(q, srec, nb, smask, slist, accr, acci);
+  }
+  fwd_epilogue<C, LOSS>(rc, q, tile, accr, acci, U, il, red);
 }
 
 #ifndef CGH_ITEMS_ONLY
@@ -509,6 +543,7 @@ __global__ void __launch_bounds__(256) k_raster_fwd(RasterConsts rc, const float
                            smask, slist, &il, red);
 }
 #endif  // CGH_ITEMS_ONLY
+
 
 // Warp reduce-scatter of COUNT values per lane (COUNT a power of two <= 32): at each step
 // lanes exchange half of their values with the partner OFF lanes away and keep the sum of
