@@ -54,6 +54,13 @@ struct RegPlan {
 template <int N, int NB>
 constexpr size_t rows_stage_bytes() { return sizeof(float) * (size_t)NB * (N / 2); }
 
+// The zeros of the padding (and of the cropped-away seed) as -0.0: a transform input known
+// at compile time to be -0.0 lets the compiler drop the additions it enters (x + (-0.0) and
+// (-0.0) - x are exact for every x, while x + (+0.0) is not: it maps -0.0 to +0.0); the
+// results differ at most in the sign of exact zeros.
+__device__ __forceinline__ float2 nz2() { return make_float2(-0.f, -0.f); }
+__device__ __forceinline__ float4 nz4() { return make_float4(-0.f, -0.f, -0.f, -0.f); }
+
 // Offset of element (row y, position a) of a column-blocked half grid (CB columns per
 // block): ((a / CB) H + y) CB + a % CB.  For the positions a = j + r M of one pass, with M a
 // multiple of CB, this is blk_base(j, y) + r M H: the butterfly's part is computed once and
@@ -101,7 +108,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __gr
     const int y = y0 + b;
     int x;
     const bool in_img = in_window<N, F::A, CA>(j, r, ox, W, x);
-    return (in_img && y < H) ? __ldg(&src[(size_t)y * W + x]) : make_float2(0.f, 0.f);
+    return (in_img && y < H) ? __ldg(&src[(size_t)y * W + x]) : nz2();
   });
   float2 out[F::GC::MB][F::C];
   if constexpr (DB) F::rest2(v, out, buf, buf + P::BUF, tw);
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
       acc = fmaf(wd, d, acc);
       val = cscale(val, gscale * wd);
     } else {
-      val = make_float2(0.f, 0.f);
+      val = nz2();
     }
   });
   const float tot = block_sum(acc, red);
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
   reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
     int y;
     return in_window<N, F::A, CA>(j, r, oy, H, y) ? __ldg(&src[y * NB + b])
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                                                   : nz4();
   });
   // the spectrum is parked in thread-private shared-memory slots (one 16-byte load per
   // element per plane) so that the inverse passes get the registers
@@ -406,7 +413,7 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
     reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
       int y;
       return in_window<N, F::A, CA>(j, r, oy, H, y) ? __ldg(&src[y * NB + b])
-                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                                                     : nz4();
     });
     float4 S[F::GC::MB][F::C];
     if constexpr (DB) F::rest2(v, S, buf4, by, tw); else F::rest(v, S, buf4, tw);
