@@ -90,6 +90,20 @@ __device__ __forceinline__ bool in_window(int j, int r, int off, int len, int& x
   }
 }
 
+// Registers of a pass of radix R over the padded length N whose positions lie outside the
+// image window for every butterfly (aligned window only; 0 otherwise): the zero padding the
+// first pass of a forward transform leaves out (DFTZ).
+template <int N, int R, bool CA>
+constexpr unsigned outside_mask() {
+  unsigned m = 0u;
+  if (CA) {
+    constexpr int M = N / R;
+    for (int r = 0; r < R; ++r)
+      if (r * M + M <= N / 4 || r * M >= 3 * N / 4) m |= 1u << r;
+  }
+  return m;
+}
+
 template <int N, int R0, int R1, int R2, int NB, int CB, int T, bool CA>
 __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __grid_constant__ BlasmDev bl,
                                                      const float2* __restrict__ tw,
@@ -104,7 +118,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_pad_fwd(const __gr
   const int H = bl.H, W = bl.W, ox = bl.ox;
   const float2* src = in + (size_t)batch * H * W;
   float2 v[F::GA::MB][F::A];
-  reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
+  constexpr unsigned ZM = outside_mask<N, F::A, CA>();  // zero padding of the first pass
+  reg::first_from_jr<N, F::A, NB, T, false, ZM>(v, [&](int b, int j, int r) {
     const int y = y0 + b;
     int x;
     const bool in_img = in_window<N, F::A, CA>(j, r, ox, W, x);
@@ -271,7 +286,8 @@ __global__ void __launch_bounds__(T, CGH_REG_MINB(T)) kr_rows_loss(const __grid_
   const float tot = block_sum(acc, red);
   if (threadIdx.x == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   if constexpr (GRAD) {
-    reg::first_in_regs<N, F::A, NB, T, false>(u);
+    // the seed is zero outside the crop: the forward transform's first pass leaves it out
+    reg::first_in_regs<N, F::A, NB, T, false, outside_mask<N, I::C, CA>()>(u);
     float2 w[F::GC::MB][F::C];
     // block_sum's barriers follow the inverse transform's last reads of buf
     if constexpr (DB) F::rest2(u, w, buf, by, tw);
@@ -337,7 +353,8 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_fwd_planes(const __grid_const
   const int H = bl.H, Nx = bl.Nx, C = bl.C, oy = bl.oy;
   const float4* src = reinterpret_cast<const float4*>(Y + (size_t)c * H * Nx + (size_t)kb * H * CB);
   float4 v[F::GA::MB][F::A];
-  reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
+  constexpr unsigned ZM = outside_mask<N, F::A, CA>();  // zero padding of the first pass
+  reg::first_from_jr<N, F::A, NB, T, false, ZM>(v, [&](int b, int j, int r) {
     int y;
     return in_window<N, F::A, CA>(j, r, oy, H, y) ? __ldg(&src[y * NB + b])
                                                    : nz4();
@@ -410,7 +427,8 @@ __global__ void __launch_bounds__(T, MINB) kr_cols_bwd_planes(const __grid_const
       for (int i = threadIdx.x; i * 128 < H * CB * 8; i += T) prefetch_l2(nxt + i * 128);
     }
     float4 v[F::GA::MB][F::A];
-    reg::first_from_jr<N, F::A, NB, T, false>(v, [&](int b, int j, int r) {
+    constexpr unsigned ZM = outside_mask<N, F::A, CA>();  // zero padding of the first pass
+    reg::first_from_jr<N, F::A, NB, T, false, ZM>(v, [&](int b, int j, int r) {
       int y;
       return in_window<N, F::A, CA>(j, r, oy, H, y) ? __ldg(&src[y * NB + b])
                                                      : nz4();

@@ -282,6 +282,177 @@ struct DFT {
   }
 };
 
+// ---------------------------------------------------------------- zero-aware codelets
+// DFTZ<R, INV, ZM>::run(v) is DFT<R, INV>::run(v) for inputs of which those with bit r of ZM
+// set are known to be zero (the zero padding of a first pass): the additions and products such
+// an input would enter are left out.  Leaving out x + 0 or y + s 0 changes no result except,
+// possibly, the sign of an exact zero; results that are zero only because all their inputs
+// are get an explicit zero.  With ZM = 0 it is DFT<R, INV> itself.
+template <class E>
+__device__ __forceinline__ E czero() {
+  E z;
+  if constexpr (sizeof(E) == sizeof(float2)) z = E{0.f, 0.f};
+  else z = E{0.f, 0.f, 0.f, 0.f};
+  return z;
+}
+__device__ __forceinline__ float2 cneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float4 cneg(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+// a + b, a - b and y + s x with compile-time zero flags of the operands
+template <bool ZA, bool ZB, class E>
+__device__ __forceinline__ E zadd(const E& a, const E& b) {
+  if constexpr (ZA && ZB) return czero<E>();
+  else if constexpr (ZA) return b;
+  else if constexpr (ZB) return a;
+  else return cadd(a, b);
+}
+template <bool ZA, bool ZB, class E>
+__device__ __forceinline__ E zsub(const E& a, const E& b) {
+  if constexpr (ZA && ZB) return czero<E>();
+  else if constexpr (ZA) return cneg(b);
+  else if constexpr (ZB) return a;
+  else return csub(a, b);
+}
+template <bool ZX, bool ZY, class E>
+__device__ __forceinline__ E zaxpy(float sc, const E& x, const E& y) {
+  if constexpr (ZX && ZY) return czero<E>();
+  else if constexpr (ZX) return y;
+  else if constexpr (ZY) return cscale(x, sc);
+  else return caxpy(sc, x, y);
+}
+
+template <int R, bool INV, unsigned ZM>
+struct DFTZ;
+
+template <bool INV, unsigned ZM>
+struct DFTZ<2, INV, ZM> {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[2]) {
+    constexpr bool z0 = ZM & 1u, z1 = ZM & 2u;
+    const E a = v[0], b = v[1];
+    v[0] = zadd<z0, z1>(a, b);
+    v[1] = zsub<z0, z1>(a, b);
+  }
+};
+
+template <bool INV, unsigned ZM>
+struct DFTZ<3, INV, ZM> {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[3]) {
+    constexpr bool z0 = ZM & 1u, z1 = ZM & 2u, z2 = ZM & 4u;
+    constexpr float h = 0.86602540378443864676f;  // sin(2 pi / 3)
+    constexpr bool zt = z1 && z2;                // t1 and t2 are zero
+    const E t1 = zadd<z1, z2>(v[1], v[2]);
+    const E t2 = mul_mi<INV>(cscale(zsub<z1, z2>(v[1], v[2]), h));
+    const E m = zaxpy<zt, z0>(-0.5f, t1, v[0]);
+    v[0] = zadd<z0, zt>(v[0], t1);
+    v[1] = zadd<zt && z0, zt>(m, t2);
+    v[2] = zsub<zt && z0, zt>(m, t2);
+  }
+};
+
+template <bool INV, unsigned ZM>
+struct DFTZ<4, INV, ZM> {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[4]) {
+    constexpr bool z0 = ZM & 1u, z1 = ZM & 2u, z2 = ZM & 4u, z3 = ZM & 8u;
+    const E t0 = zadd<z0, z2>(v[0], v[2]), t1 = zsub<z0, z2>(v[0], v[2]);
+    const E t2 = zadd<z1, z3>(v[1], v[3]), t3 = mul_mi<INV>(zsub<z1, z3>(v[1], v[3]));
+    constexpr bool za = z0 && z2, zb = z1 && z3;
+    v[0] = zadd<za, zb>(t0, t2);
+    v[2] = zsub<za, zb>(t0, t2);
+    v[1] = zadd<za, zb>(t1, t3);
+    v[3] = zsub<za, zb>(t1, t3);
+  }
+};
+
+template <bool INV, unsigned ZM>
+struct DFTZ<5, INV, ZM> {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[5]) {
+    constexpr bool z0 = ZM & 1u, z1 = ZM & 2u, z2 = ZM & 4u, z3 = ZM & 8u, z4 = ZM & 16u;
+    constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+    constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+    constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+    constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+    constexpr bool zad = z1 && z4, zcd = z2 && z3;  // a, b zero; c, d zero
+    const E a = zadd<z1, z4>(v[1], v[4]), b = zsub<z1, z4>(v[1], v[4]);
+    const E c = zadd<z2, z3>(v[2], v[3]), d = zsub<z2, z3>(v[2], v[3]);
+    const E x0 = v[0];
+    constexpr bool zr = zad && zcd && z0, zi = zad && zcd;
+    const E r1 = zaxpy<zcd, zad && z0>(c2, c, zaxpy<zad, z0>(c1, a, x0));
+    const E r2 = zaxpy<zcd, zad && z0>(c1, c, zaxpy<zad, z0>(c2, a, x0));
+    const E i1 = mul_mi<INV>(zaxpy<zcd, zad>(s2, d, zad ? czero<E>() : cscale(b, s1)));
+    const E i2 = mul_mi<INV>(zaxpy<zcd, zad>(-s1, d, zad ? czero<E>() : cscale(b, s2)));
+    v[0] = zadd<z0, zi>(x0, zadd<zad, zcd>(a, c));
+    v[1] = zadd<zr, zi>(r1, i1);
+    v[4] = zsub<zr, zi>(r1, i1);
+    v[2] = zadd<zr, zi>(r2, i2);
+    v[3] = zsub<zr, zi>(r2, i2);
+  }
+};
+
+// zero mask of the inner (A-point) DFT for group n2 of a composite R = A B, and of the groups
+// whose inputs are all zero (their outputs, inputs of the outer B-point DFTs, are zero too)
+template <int R, int A, int B, unsigned ZM>
+constexpr unsigned dftz_inner_mask(int n2, bool pfa) {
+  unsigned m = 0;
+  for (int n1 = 0; n1 < A; ++n1) {
+    const int n = pfa ? (B * n1 + A * n2) % R : B * n1 + n2;
+    if ((ZM >> n) & 1u) m |= 1u << n1;
+  }
+  return m;
+}
+template <int R, int A, int B, unsigned ZM>
+constexpr unsigned dftz_outer_mask(bool pfa) {
+  unsigned m = 0;
+  for (int n2 = 0; n2 < B; ++n2)
+    if (dftz_inner_mask<R, A, B, ZM>(n2, pfa) == (1u << A) - 1u) m |= 1u << n2;
+  return m;
+}
+
+// composite R = A B, the structure of DFT<R, INV> with the masks carried into its parts
+template <int R, bool INV, unsigned ZM>
+struct DFTZ {
+  template <class E>
+  __device__ __forceinline__ static void run(E (&v)[R]) {
+    if constexpr (ZM == 0u) {
+      DFT<R, INV>::run(v);
+    } else {
+      constexpr int A = SplitOf<R>::A, B = SplitOf<R>::B;
+      constexpr bool pfa = gcd_c(A, B) == 1;
+      constexpr unsigned ZO = dftz_outer_mask<R, A, B, ZM>(pfa);
+      E u[B][A];
+      sfor<0, B>([&](auto N2) {
+        constexpr int n2 = decltype(N2)::value;
+        constexpr unsigned zi = dftz_inner_mask<R, A, B, ZM>(n2, pfa);
+        E t[A];
+        sfor<0, A>([&](auto N1) {
+          constexpr int n1 = decltype(N1)::value;
+          t[n1] = pfa ? v[(B * n1 + A * n2) % R] : v[B * n1 + n2];
+        });
+        DFTZ<A, INV, zi>::run(t);
+        sfor<0, A>([&](auto K1) {
+          constexpr int k1 = decltype(K1)::value;
+          if constexpr (pfa || ((ZO >> n2) & 1u)) u[n2][k1] = t[k1];
+          else u[n2][k1] = twmul<n2 * k1, R, INV>(t[k1]);
+        });
+      });
+      constexpr int eA = pfa ? B * inv_mod(B % A, A) : 0, eB = pfa ? A * inv_mod(A % B, B) : 0;
+      sfor<0, A>([&](auto K1) {
+        constexpr int k1 = decltype(K1)::value;
+        E t[B];
+        sfor<0, B>([&](auto N2) { t[decltype(N2)::value] = u[decltype(N2)::value][k1]; });
+        DFTZ<B, INV, ZO>::run(t);
+        sfor<0, B>([&](auto K2) {
+          constexpr int k2 = decltype(K2)::value;
+          if constexpr (pfa) v[(eA * k1 + eB * k2) % R] = t[k2];
+          else v[k1 + A * k2] = t[k2];
+        });
+      });
+    }
+  }
+};
+
 // ---------------------------------------------------------------- CTA-level transform
 __device__ __forceinline__ int sidx(int i) { return i + (i >> 4); }
 

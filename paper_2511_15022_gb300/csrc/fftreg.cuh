@@ -104,7 +104,9 @@ __device__ __forceinline__ void first_from(E (&v)[Geo<N, R, NB, T>::MB][R], F&& 
 // Same with the functor called as f(b, j, r) for position j + r N/R, r a constant after
 // unrolling: terms of an address that depend only on (b, j) are then computed once per
 // butterfly, the r-dependent part folds into a constant or one multiply-add.
-template <int N, int R, int NB, int T, bool INV, class E, class F>
+// ZM: registers known to be zero in every butterfly (bit r: position j + r N/R is outside the
+// data for every j), whose arithmetic the pass leaves out (DFTZ); f is not called for them.
+template <int N, int R, int NB, int T, bool INV, unsigned ZM = 0u, class E, class F>
 __device__ __forceinline__ void first_from_jr(E (&v)[Geo<N, R, NB, T>::MB][R], F&& f) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
@@ -113,20 +115,22 @@ __device__ __forceinline__ void first_from_jr(E (&v)[Geo<N, R, NB, T>::MB][R], F
     if (valid<N, R, NB, T>(q)) {
       const int b = (int)((unsigned)q % NB), j = (int)((unsigned)q / NB);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i][r] = f(b, j, r);
-      DFT<R, INV>::run(v[i]);
+      for (int r = 0; r < R; ++r)
+        if (!((ZM >> r) & 1u)) v[i][r] = f(b, j, r);
+      DFTZ<R, INV, ZM>::run(v[i]);
     }
   }
 }
 
-// First pass (Ns = 1) on values already in registers at positions j + r N/R.
-template <int N, int R, int NB, int T, bool INV, class E>
+// First pass (Ns = 1) on values already in registers at positions j + r N/R (ZM: registers
+// known to be zero, as for first_from_jr).
+template <int N, int R, int NB, int T, bool INV, unsigned ZM = 0u, class E>
 __device__ __forceinline__ void first_in_regs(E (&v)[Geo<N, R, NB, T>::MB][R]) {
   using G = Geo<N, R, NB, T>;
 #pragma unroll
   for (int i = 0; i < G::MB; ++i) {
     const int q = threadIdx.x + i * T;
-    if (valid<N, R, NB, T>(q)) DFT<R, INV>::run(v[i]);
+    if (valid<N, R, NB, T>(q)) DFTZ<R, INV, ZM>::run(v[i]);
   }
 }
 
