@@ -573,6 +573,53 @@ struct ReduceScatter<1, OFF> {
   }
 };
 
+// The same for exactly 12 values per lane (C = 3): 13 shuffles instead of the 16 of the padded
+// 16-value form.  After halving twice (6, then 3 values) the three values split unevenly --
+// lanes with bit 2 clear keep values 0 and 1, lanes with bit 2 set keep value 2 -- and one more
+// exchange leaves one value per lane.  Lane value index: (lane & 16 ? 6 : 0) + (lane & 8 ? 3 : 0)
+// + (lane & 4 ? 2 : lane & 2 ? 1 : 0); it owns the value (adds it out) when bit 0 is clear and
+// not both bits 2 and 1 are set.
+__device__ __forceinline__ void reduce_scatter_12(float* cur, int lane, int& vidx,
+                                                  bool& owner) {
+  {  // 12 -> 6
+    const bool hi = (lane & 16) != 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const float send = hi ? cur[i] : cur[i + 6];
+      const float keep = hi ? cur[i + 6] : cur[i];
+      cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {  // 6 -> 3
+    const bool hi = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const float send = hi ? cur[i] : cur[i + 3];
+      const float keep = hi ? cur[i + 3] : cur[i];
+      cur[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  const bool b2 = (lane & 4) != 0, b1 = (lane & 2) != 0;
+  {  // 3 -> {0, 1} (bit 2 clear) or {2} (bit 2 set)
+    const float r0 = __shfl_xor_sync(0xffffffffu, b2 ? cur[0] : cur[2], 4);
+    const float r1 = __shfl_xor_sync(0xffffffffu, cur[1], 4);
+    if (b2) {
+      cur[0] = cur[2] + r0;
+    } else {
+      cur[0] += r0;
+      cur[1] += r1;
+    }
+  }
+  {  // -> one value: {0} / {1} by bit 1 (bit 2 clear), {2} on both partners (bit 2 set)
+    const float send = b2 ? cur[0] : (b1 ? cur[0] : cur[1]);
+    const float keep = b2 ? cur[0] : (b1 ? cur[1] : cur[0]);
+    cur[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  cur[0] += __shfl_xor_sync(0xffffffffu, cur[0], 1);
+  vidx = ((lane & 16) ? 6 : 0) + ((lane & 8) ? 3 : 0) + (b2 ? 2 : (b1 ? 1 : 0));
+  owner = (lane & 1) == 0 && !(b2 && b1);
+}
+
 // Raw accumulated moments per Gaussian (NV = 2C + 6 values):
 //   [0, C)      P_c = sum a dL/dRe_c          [C, 2C)  Q_c = sum a dL/dIm_c
 //   2C          SG  = sum G S (unclamped pairs), S = sum_c (A_c dRe_c + B_c dIm_c)
@@ -848,9 +895,15 @@ __device__ __forceinline__ void raster_bwd_region(const RasterConsts& rc,
         }
       }
       int vidx = 0;
-      ReduceScatter<NVP, 16>::run(acc, lane, vidx);
-      if ((lane & (32 / NVP - 1)) == 0 && vidx < NV && acc[0] != 0.f)
-        atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
+      if constexpr (NV == 12) {
+        bool owner;
+        reduce_scatter_12(acc, lane, vidx, owner);
+        if (owner && acc[0] != 0.f) atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
+      } else {
+        ReduceScatter<NVP, 16>::run(acc, lane, vidx);
+        if ((lane & (32 / NVP - 1)) == 0 && vidx < NV && acc[0] != 0.f)
+          atomicAdd(&raw[(size_t)sgid[j] * CGH_RAW_STRIDE + vidx], acc[0]);
+      }
     }
   }
 }
