@@ -197,8 +197,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the FFT passes of the timed 1080 x 1920 hologram (padded 2160 x 3840) are specialised in
+# blasm_spec_a.cu; the other blasm_spec_*.cu files hold other lengths only
 FFT_SOURCES = ("fft.cuh", "fftreg.cuh", "blasm_common.cuh", "blasm_reg.cuh", "blasm_spec.h",
-               "blasm_spec_*.cu", "blasm.cu", "blasm_generic.cuh", "cgh_internal.h")
+               "blasm_spec_a.cu", "blasm.cu", "blasm_generic.cuh", "cgh_internal.h")
 RASTER_SOURCES = ("raster.cu", "raster.cuh", "cgh_internal.h")
 
 

@@ -552,14 +552,20 @@ cudaError_t reg_rows_launch(int kind, const cgh_plan* p, const SpecRowArgs* a, c
   return reg_rows_launch_ca<N, R0, R1, R2, NB, CB, T, false>(kind, p, a, bl, s);
 }
 
-template <int N, int R0, int R1, int R2, int NB, int T, int MINBF, int MINBB, bool CA>
+// (R0, R1, R2): radix order of the forward-model kernel; (Q0, Q1, Q2): that of the adjoint one
+// (each kernel runs its own complete transforms, so the two orders are independent).
+template <int N, int R0, int R1, int R2, int Q0, int Q1, int Q2, int NB, int T, int MINBF,
+          int MINBB, bool CA>
 cudaError_t reg_cols_launch_ca(int kind, const cgh_plan* p, const BlasmDev& bl, const float2* in,
                                float2* out, cudaStream_t s) {
   using P = RegPlan<N, R0, R1, R2, NB, T, float4>;
+  using PB = RegPlan<N, Q0, Q1, Q2, NB, T, float4>;
   static_assert(P::F::C == P::I::A, "slot layout shared by the forward end and inverse start");
+  static_assert(PB::F::C == PB::I::A, "slot layout shared by the forward end and inverse start");
   constexpr int MINB = MINBF;  // in-band forward kernel
   constexpr size_t smem = P::db_fits(MINB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
-  constexpr size_t smem_b = P::db_fits(MINBB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
+  constexpr size_t smem_m = P::db_fits(MINBB) ? P::SMEM_SLOTS_DB : P::SMEM_SLOTS;
+  constexpr size_t smem_b = PB::db_fits(MINBB) ? PB::SMEM_SLOTS_DB : PB::SMEM_SLOTS;
   dim3 grid(bl.Nx / (2 * NB), p->C);
   const float2* tw = p->fy.tw;
   cudaError_t e = cudaSuccess;
@@ -573,15 +579,15 @@ cudaError_t reg_cols_launch_ca(int kind, const cgh_plan* p, const BlasmDev& bl, 
     // MINBF applies to the in-band form (the masked one keeps the general residency)
     auto k = all_in ? kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINB, true, CA>
                     : kr_cols_fwd_planes<N, R0, R1, R2, NB, T, MINBB, false, CA>;
-    const size_t sm = all_in ? smem : smem_b;
+    const size_t sm = all_in ? smem : smem_m;
     e = reg_set_smem(k, sm, all_in ? MINB : MINBB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_FWD_PLANES, s);
     k<<<grid, T, sm, s>>>(bl, tw, in, out);
     prof_end(KID_COLS_FWD_PLANES, s);
   } else {
-    auto k = all_in ? kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINBB, true, CA>
-                    : kr_cols_bwd_planes<N, R0, R1, R2, NB, T, MINBB, false, CA>;
+    auto k = all_in ? kr_cols_bwd_planes<N, Q0, Q1, Q2, NB, T, MINBB, true, CA>
+                    : kr_cols_bwd_planes<N, Q0, Q1, Q2, NB, T, MINBB, false, CA>;
     e = reg_set_smem(k, smem_b, MINBB);
     if (e != cudaSuccess) return e;
     prof_begin(KID_COLS_BWD_PLANES, s);
@@ -595,13 +601,16 @@ cudaError_t reg_cols_launch_ca(int kind, const cgh_plan* p, const BlasmDev& bl, 
 // oy = N / 4) and in the general form.
 // MINBA: resident CTAs per SM of the aligned-window, in-band forward kernel (its dead cropped
 // outputs and known zero inputs free registers, so it can fit more CTAs than the others).
-template <int N, int R0, int R1, int R2, int NB, int T, int MINB, int MINBA>
+template <int N, int R0, int R1, int R2, int Q0, int Q1, int Q2, int NB, int T, int MINB,
+          int MINBA>
 cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, const float2* in,
                             float2* out, cudaStream_t s) {
   const BlasmDev& bl = blp ? *blp : p->bl;
   if (2 * bl.H == N && 4 * bl.oy == N)
-    return reg_cols_launch_ca<N, R0, R1, R2, NB, T, MINBA, MINB, true>(kind, p, bl, in, out, s);
-  return reg_cols_launch_ca<N, R0, R1, R2, NB, T, MINB, MINB, false>(kind, p, bl, in, out, s);
+    return reg_cols_launch_ca<N, R0, R1, R2, Q0, Q1, Q2, NB, T, MINBA, MINB, true>(kind, p, bl,
+                                                                                  in, out, s);
+  return reg_cols_launch_ca<N, R0, R1, R2, Q0, Q1, Q2, NB, T, MINB, MINB, false>(kind, p, bl, in,
+                                                                                out, s);
 }
 
 }  // namespace cgh
@@ -617,9 +626,13 @@ cudaError_t reg_cols_launch(int kind, const cgh_plan* p, const BlasmDev* blp, co
 //   SM the registers are sized for.
 #define CGH_COL_SPEC(N, R0, R1, R2, NB, T, MINB) CGH_COL_SPEC_A(N, R0, R1, R2, NB, T, MINB, MINB)
 //   ... with MINBA resident CTAs for the aligned-window forward kernel
-#define CGH_COL_SPEC_A(N, R0, R1, R2, NB, T, MINB, MINBA)                                    \
+#define CGH_COL_SPEC_A(N, R0, R1, R2, NB, T, MINB, MINBA) \
+  CGH_COL_SPEC_FB(N, R0, R1, R2, R0, R1, R2, NB, T, MINB, MINBA)
+//   ... with radix order (Q0, Q1, Q2) for the adjoint kernel
+#define CGH_COL_SPEC_FB(N, R0, R1, R2, Q0, Q1, Q2, NB, T, MINB, MINBA)                       \
   if (N_ == N && CB_ == 2 * (NB)) {                                                         \
     if (!dry)                                                                               \
-      *err = cgh::reg_cols_launch<N, R0, R1, R2, NB, T, MINB, MINBA>(kind, p, bl, in, out, s); \
+      *err = cgh::reg_cols_launch<N, R0, R1, R2, Q0, Q1, Q2, NB, T, MINB, MINBA>(kind, p, bl, \
+                                                                               in, out, s);  \
     return true;                                                                            \
   }

@@ -10,6 +10,6 @@ bool spec_rows_f(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const Sp
 bool spec_cols_f(int kind, int N_, int CB_, const cgh_plan* p, const BlasmDev* bl,
                  const float2* in, float2* out,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_COL_SPEC(2880, 12, 15, 16, 1, 240, 2)
+  CGH_COL_SPEC(2880, 20, 12, 12, 1, 240, 2)
   return false;
 }
