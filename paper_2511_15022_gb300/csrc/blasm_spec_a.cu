@@ -4,7 +4,7 @@
 
 bool spec_rows_a(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const SpecRowArgs* a,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_ROW_SPEC(3840, 16, 16, 15, 2, 2, 512)
+  CGH_ROW_SPEC(3840, 16, 15, 16, 2, 2, 512)
   return false;
 }
 

@@ -10,6 +10,6 @@ bool spec_rows_d(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const Sp
 bool spec_cols_d(int kind, int N_, int CB_, const cgh_plan* p, const BlasmDev* bl,
                  const float2* in, float2* out,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_COL_SPEC(4320, 24, 15, 12, 1, 384, 1)
+  CGH_COL_SPEC_FB(4320, 24, 15, 12, 15, 24, 12, 1, 384, 1, 1)
   return false;
 }

@@ -11,6 +11,6 @@ bool spec_rows_g(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const Sp
 bool spec_cols_g(int kind, int N_, int CB_, const cgh_plan* p, const BlasmDev* bl,
                  const float2* in, float2* out,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_COL_SPEC_FB(3600, 16, 15, 15, 15, 16, 15, 1, 240, 2, 2)
+  CGH_COL_SPEC(3600, 15, 16, 15, 1, 240, 2)
   return false;
 }
