@@ -3,7 +3,7 @@
 
 bool spec_rows_f(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const SpecRowArgs* a,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_ROW_SPEC(5120, 16, 16, 20, 1, 2, 320)
+  CGH_ROW_SPEC(5120, 16, 20, 16, 1, 2, 320)
   return false;
 }
 

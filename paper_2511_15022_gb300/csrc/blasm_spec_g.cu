@@ -4,7 +4,7 @@
 
 bool spec_rows_g(int kind, int N_, int RB_, int CB_, const cgh_plan* p, const SpecRowArgs* a,
                  cudaStream_t s, cudaError_t* err, bool dry) {
-  CGH_ROW_SPEC(6400, 16, 20, 20, 1, 2, 416)
+  CGH_ROW_SPEC(6400, 20, 20, 16, 1, 2, 416)
   return false;
 }
 
