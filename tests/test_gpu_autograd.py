@@ -1,6 +1,7 @@
 """The torch.autograd.Function (forward recomputed in the backward pass, Sec. 3.4) on the
 GPU: loss and parameter gradients against the FP64 oracle, the upstream gradient applied
-inside the library, reuse of the forward's binning only while it is still the caller's,
+inside the library, reuse of the forward's binning only while it is still the caller's, the
+eager form (gradients computed in the forward, no recompute) against the recomputing one,
 and the gradients of a 64x64 crop of the 1080p RGB three-plane workload against central
 differences of the oracle's forward loss."""
 import numpy as np
@@ -69,6 +70,33 @@ def test_upstream_gradient_scales_every_gradient(dev):
     _, g3 = autograd_grads(plan, leaf_params(p, dev), T, scale=-2.5)
     for k in g1:
         assert rel_l2(g3[k].double().cpu().numpy(), -2.5 * g1[k].double().cpu().numpy()) < 1e-5, k
+
+
+def test_eager_mode_equals_recompute(dev):
+    """hologram_loss(..., eager=True) runs the fused forward and backward inside the autograd
+    forward and keeps only the O(N) parameter gradients, which backward multiplies by the
+    upstream scalar: the same loss and gradients as the recomputing path, scaled alike."""
+    import torch
+    from paper_2511_15022_gb300.autograd import hologram_loss
+    w = inputs.custom(80, 100, 900, wavelengths_m=RGB, z_m=PLANES, seed=41)
+    p = inputs.params_for(w)
+    T = torch.from_numpy(inputs.blob_targets(w.L, w.C, w.H, w.W)).to(dev)
+    plan = make_plan(w, dev)
+
+    def run(eager, scale):
+        params = leaf_params(p, dev)
+        loss = hologram_loss(plan, params, T, eager=eager)
+        (loss * scale).backward()
+        return loss.item(), {k: v.grad.double().cpu().numpy() for k, v in params.items()}
+
+    l0, g0 = run(False, 1.0)
+    l1, g1 = run(True, 1.0)
+    _, g2 = run(True, -2.5)
+    assert abs(l1 - l0) < 1e-5 * abs(l0)
+    for k in g0:
+        assert rel_l2(g1[k], g0[k]) < 1e-5, k
+        # separate steps: the raster backward's atomics add in a different order each run
+        assert rel_l2(g2[k], -2.5 * g1[k]) < 1e-5, k
 
 
 def test_binning_reuse_equals_rebinning(dev):
